@@ -1,0 +1,420 @@
+#!/usr/bin/env python
+"""Mojette encode/decode benchmark on GB300 (one JSON line on rank 0).
+
+Workload (default "plain_at_scale"): 262144 stripes of 8 KB (Q = 4 lines of
+P = 256 uint64 pixels, uniform random from a seed), n = 6 projections with
+p in {-3,-2,-1,1,2,3}. One step = encode every stripe, then decode every
+stripe under each of the 15 two-erasure patterns (16 kernel launches).
+Metric: user-data GB/s = stripes * 8192 B * 16 / step time.
+
+Timing: W warm-up steps, then K steps between a barrier + synchronize on
+both sides, CUDA events on the launching stream around every launch, max
+over ranks. Inputs (2.1 GB image, 3.3 GB projections) exceed the 129 MB L2,
+so no flush is needed between steps.
+
+--impl reference times the CPU oracle (the slow plain implementation the
+tests compare against) on the host cores, on bounded samples of the same
+workload: it is the reported baseline arm, not a target.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1504_07038_gb300 import inputs  # noqa: E402
+
+SIX = [-3, -2, -1, 1, 2, 3]
+TWELVE = [v for v in range(-6, 7) if v]
+WORKLOADS = {
+    "plain_at_scale": dict(P=256, Q=4, p=SIX, S=262144, erasures=2,
+                           desc="262144 stripes x 8 KB (Q=4, P=256 uint64), (6,4) p=+-1..3; "
+                                "encode + decode under all 15 two-erasure masks"),
+    "profile_8k": dict(P=256, Q=4, p=SIX, S=32768, erasures=2, mask_sample=1,
+                       desc="32768 stripes x 8 KB (Q=4, P=256), (6,4); encode + 1 two-erasure decode "
+                            "(small case for ncu captures; 268 MB image > L2)"),
+    "plain": dict(P=128, Q=4, p=SIX, S=1024, erasures=2,
+                  desc="1024 stripes x 4 KB (Q=4, P=128), (6,4); encode + 15 two-erasure decodes"),
+    "wide_4k": dict(P=64, Q=8, p=TWELVE, S=262144, erasures=4, mask_sample=15,
+                    desc="262144 stripes x 4 KB (Q=8, P=64), (12,8); encode + 15 four-erasure decodes"),
+    "wide_8k": dict(P=128, Q=8, p=TWELVE, S=262144, erasures=4, mask_sample=15,
+                    desc="262144 stripes x 8 KB (Q=8, P=128), (12,8); encode + 15 four-erasure decodes"),
+}
+METRIC = "Mojette encode/decode user-data GB/s & % HBM roofline; batched vs plain, 1 GB300"
+KERNEL_SOURCES = ["encode.cu", "decode.cu", "ptx.cuh", "mojette_internal.h"]
+
+
+def workload_masks(w):
+    n = len(w["p"])
+    ms = inputs.all_masks(n, w["erasures"])
+    k = w.get("mask_sample")
+    if k and len(ms) > k:
+        ms = ms[:: len(ms) // k][:k]
+    return ms
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1504_07038_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload][kernel]
+        if e.get("kernel_hash") != kernel_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        rows = []
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.uuid and parts[1] != self.uuid and len({r.split(",")[1] for r in self.lines if "," in r}) > 1:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower() == "active"})
+        loaded = [v for v in sm if smax and v > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def run_gpu(args, w):
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    P, Q, p, S = w["P"], w["Q"], w["p"], w["S"]
+    masks = workload_masks(w)
+    plan = mj.mojette_plan(P, Q, p)
+    stream = torch.cuda.current_stream()
+
+    img_np = inputs.stripes(S, Q, P, first=rank * S)     # each rank its own stripes
+    h_img = torch.from_numpy(img_np.view(np.int64)).pin_memory()
+    del img_np
+    d_img = h_img.cuda()
+    d_proj = torch.empty((S, plan.total), dtype=torch.int64, device="cuda")
+    d_out = torch.empty((S, Q, P), dtype=torch.int64, device="cuda")
+    launches_per_step = 1 + len(masks)
+
+    def mk():
+        return torch.cuda.Event(enable_timing=True)
+
+    def step(ev=None):
+        """One step; ev: list of (start, end) event pairs, one per launch."""
+        if ev:
+            ev[0][0].record(stream)
+        mj.mojette_encode(plan, d_img, d_proj, S, stream)
+        if ev:
+            ev[0][1].record(stream)
+        for k, m in enumerate(masks):
+            if ev:
+                ev[1 + k][0].record(stream)
+            mj.mojette_decode(plan, d_proj, m, d_out, S, stream)
+            if ev:
+                ev[1 + k][1].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    mj.mojette_device_status()        # raises if any bounded wait expired
+    barrier()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    events = [[(mk(), mk()) for _ in range(launches_per_step)] for _ in range(args.steps)]
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.4)
+    t0, t1 = mk(), mk()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(events[k])
+    t1.record(stream)
+    barrier()
+    enc_ms = [e[0][0].elapsed_time(e[0][1]) for e in events]
+    dec_ms = [a.elapsed_time(b) for e in events for a, b in e[1:]]
+    total_ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    mj.mojette_device_status()
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None if args.no_e2e else run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return None
+
+    user_bytes = S * Q * P * 8
+    ms_step = total_ms / args.steps
+    value = world * user_bytes * launches_per_step / (ms_step * 1e-3) / 1e9
+    enc_ms_avg = statistics.mean(enc_ms)
+    dec_ms_avg = statistics.mean(dec_ms)
+    enc_bytes = S * (Q * P + plan.total) * 8
+    dec_bytes = S * 2 * Q * P * 8
+    peak, peak_kind = measured_peaks()
+    dec_gbs = dec_bytes / (dec_ms_avg * 1e-3) / 1e9
+    enc_gbs = enc_bytes / (enc_ms_avg * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic (seeded SplitMix64 uniform uint64 pixels)",
+        "config": {"workload": args.workload, "description": w["desc"], "stripes": S,
+                   "block_bytes": Q * P * 8, "Q": Q, "P": P, "n": len(p), "p": p,
+                   "decode_masks": len(masks), "launches_per_step": launches_per_step,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "decode_lines", "achieved": round(dec_gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
+                     "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
+                     "traffic": ncu_traffic("decode_lines", args.workload),
+                     "algorithmic_bytes_per_launch": dec_bytes},
+        "kernels": {
+            "encode_tiles": {"ms": round(enc_ms_avg, 4), "hbm_gbs": round(enc_gbs, 1),
+                             "frac": round(enc_gbs / peak, 4),
+                             "user_gbs": round(user_bytes / (enc_ms_avg * 1e-3) / 1e9, 1),
+                             "algorithmic_bytes_per_launch": enc_bytes,
+                             "traffic": ncu_traffic("encode_tiles", args.workload)},
+            "decode_lines": {"ms": round(dec_ms_avg, 4), "hbm_gbs": round(dec_gbs, 1),
+                             "frac": round(dec_gbs / peak, 4),
+                             "user_gbs": round(user_bytes / (dec_ms_avg * 1e-3) / 1e9, 1),
+                             "algorithmic_bytes_per_launch": dec_bytes},
+        },
+        "gpu_launches": args.steps * launches_per_step,
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, masks, budget_s=args.cpu_seconds)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
+    """Same metric through the C ABI with host buffers: every step copies the
+    image in and the projections out (encode), then for each mask the
+    projections in and the image out (decode), from/to pinned host memory."""
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
+
+    S, Q, P = w["S"], w["Q"], w["P"]
+    h_proj = torch.empty((S, plan.total), dtype=torch.int64).pin_memory()
+    h_out = torch.empty((S, Q, P), dtype=torch.int64).pin_memory()
+
+    def step():
+        d_img.copy_(h_img, non_blocking=True)
+        mj.mojette_encode(plan, d_img, d_proj, S, stream)
+        h_proj.copy_(d_proj, non_blocking=True)
+        for m in masks:
+            d_proj.copy_(h_proj, non_blocking=True)
+            mj.mojette_decode(plan, d_proj, m, d_out, S, stream)
+            h_out.copy_(d_out, non_blocking=True)
+
+    steps = max(1, min(args.steps, 3))
+    step()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    ok = bool(np.array_equal(h_out[: min(S, 64)].numpy(), h_img[: min(S, 64)].numpy()))
+    user = S * Q * P * 8 * (1 + len(masks))
+    return {"value": round(user / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
+            "h2d_bytes_per_step": S * Q * P * 8 + len(masks) * S * plan.total * 8,
+            "d2h_bytes_per_step": S * plan.total * 8 + len(masks) * S * Q * P * 8,
+            "ms_per_step": round(ms, 3), "steps": steps, "round_trip_ok": ok}
+
+
+# --------------------------------------------------------------- CPU oracle --
+
+def cpu_baseline(w, masks, budget_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload (1 encode + len(masks) decodes per stripe, like a step)."""
+    import oracle
+    P, Q, p = w["P"], w["Q"], w["p"]
+    cores = os.cpu_count() or 1
+    S = 64
+    while True:
+        img = inputs.stripes(S, Q, P)
+        t0 = time.perf_counter()
+        proj = oracle.encode(img, p, threads=cores)
+        for m in masks:
+            oracle.decode(proj, p, P, Q, m, threads=cores)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or S >= w["S"]:
+            break
+        S = min(w["S"], int(S * max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    user = S * Q * P * 8 * (1 + len(masks))
+    cpu = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    cpu = ln.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return {"value": round(user / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{S} stripes of the workload: 1 encode + {len(masks)} decodes each "
+                      f"({dt:.1f} s, {cores} threads, cpu {cpu})"}
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    masks = workload_masks(w)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_baseline(w, masks, budget_s=per_step)
+    vals = [cpu_baseline(w, masks, budget_s=per_step) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    user_step = w["S"] * w["Q"] * w["P"] * 8 * (1 + len(masks))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(user_step / (v * 1e9) * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (seeded SplitMix64 uniform uint64 pixels)",
+            "config": {"workload": args.workload, "description": w["desc"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain_at_scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    w = WORKLOADS[args.workload]
+    line = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * mojette.h -- C ABI of libmojette, a GB300 (sm_103a) implementation of the
+ * Mojette erasure code over GF(2): the forward Mojette transform (encode)
+ * and its inverse (decode).
+ *
+ * Notation (Pertin et al., "Performance evaluation of the Mojette erasure
+ * code for fault-tolerant distributed hot data storage"):
+ *   - A stripe is a P x Q image f(x, l) of 64-bit pixels: Q data lines (the
+ *     code's k, Sec. 2.3) of P pixels each, stored row-major as
+ *     img[l * P + x] (x the column, l the line). S stripes lie back to back.
+ *   - Projection i has direction (p_i, 1) (q_i = 1, Sec. 2.3). Its bin at
+ *     position b is the XOR of the pixels on the discrete line b = l p_i - x
+ *     (Eq. 1 with XOR as the addition, Sec. 3). It has
+ *     B_i = |p_i| (Q - 1) + P bins (Eq. 2), stored at j = b - b_min_i with
+ *     b_min_i = -(P - 1) + min(0, (Q - 1) p_i).
+ *   - A stripe's projections are concatenated in the order the directions
+ *     were given: proj[s * total + off_i + j], off_i = sum_{i' < i} B_i',
+ *     total = sum_i B_i. A storage node would hold one projection slice.
+ *
+ * Conventions for every call:
+ *   - Return value: 0 on success or a negative errno:
+ *       -EINVAL           bad geometry or argument (P, Q, n out of range,
+ *                         duplicate directions, null pointer, S < 0);
+ *       -ERANGE           a device pointer that is not 16-byte aligned;
+ *       -ENOTRECOVERABLE  the surviving projections cannot rebuild the image;
+ *       -ENOMEM           host or device allocation failed;
+ *       -EIO              a CUDA runtime error (see mojette_last_cuda_error);
+ *       -ETIMEDOUT        a bounded device-side wait expired (reported by
+ *                         mojette_device_status).
+ *   - Device buffers (d_*) are owned by the caller, live in the current
+ *     device's memory, and must not overlap each other. Work is enqueued on
+ *     `stream` (a cudaStream_t; NULL = legacy default stream) and is
+ *     asynchronous: the caller synchronises before reading results.
+ *   - Plans are owned by the library from mojette_plan until
+ *     mojette_plan_destroy. A plan may be used from several host threads at
+ *     once; its schedule cache is internally locked. Per-device resources
+ *     (reconstruction schedules) are created on first use on each device,
+ *     with a blocking copy: make that first call outside any stream capture.
+ */
+#ifndef MOJETTE_H
+#define MOJETTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; declared here so this header needs no CUDA
+ * header. */
+typedef struct CUstream_st *mojette_stream_t;
+
+/* Opaque plan: geometry, bin layout and the reconstruction-schedule cache. */
+typedef struct mojette_plan_s *mojette_plan_t;
+
+/* Largest number of projections a plan may hold (erasure masks are 32-bit). */
+#define MOJETTE_MAX_PROJECTIONS 32
+/* Largest Q the decoder accepts (one lane per data line, Sec. 2.2). */
+#define MOJETTE_MAX_DECODE_LINES 16
+
+/*
+ * mojette_plan -- validate a geometry and compute its bin layout.
+ * Defines: Sec. 2.1 (Eq. 1, Eq. 2) for the layout, Sec. 2.3 for q_i = 1.
+ *   P, Q   image width (pixels per line, >= 1) and number of lines (>= 1);
+ *   p[n]   the directions p_i of the n projections (1 <= n <= 32), distinct
+ *          integers (p = 0 allowed); read, not retained;
+ *   out    receives the plan.
+ * Host only: touches no device. Errors: -EINVAL, -ENOMEM.
+ */
+int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out);
+
+/* Release a plan and every host and device resource it holds. Must not be
+ * called while work that uses the plan is still in flight. NULL is a no-op. */
+int mojette_plan_destroy(mojette_plan_t plan);
+
+/*
+ * mojette_plan_info -- the bin layout (Eq. 2).
+ *   bins[n], offsets[n]  receive B_i and off_i (either may be NULL);
+ *   total                receives sum_i B_i, the words per encoded stripe
+ *                        (may be NULL).
+ */
+int mojette_plan_info(mojette_plan_t plan, int64_t *bins, int64_t *offsets,
+                      int64_t *total);
+
+/*
+ * mojette_encode -- forward Mojette transform of S stripes (Sec. 2.1, Eq. 1;
+ * XOR addition, Sec. 3).
+ *   d_img   [S][Q][P] uint64 pixels, read;
+ *   d_proj  [S][total] uint64 bins, written (every bin, empty ones as 0);
+ *   S       number of stripes (0 is a no-op).
+ * Both pointers must be 16-byte aligned. Errors: -EINVAL, -ERANGE, -EIO.
+ */
+int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
+                   int64_t S, mojette_stream_t stream);
+
+/*
+ * mojette_decode -- inverse Mojette transform of S stripes that all lost the
+ * same projections (Sec. 2.2; Sec. 2.3 for "any Q of the n projections").
+ *   d_proj        [S][total] uint64 bins, read; the slices of erased
+ *                 projections are never read (their contents do not matter);
+ *   erasure_mask  bit i set: projection i is lost;
+ *   d_img         [S][Q][P] uint64 pixels, written.
+ * At least Q projections must survive, and Q <= MOJETTE_MAX_DECODE_LINES;
+ * otherwise -ENOTRECOVERABLE (resp. -EINVAL). The reconstruction path for
+ * the surviving set is computed on the host on first use and cached in the
+ * plan (the paper's pre-determined path, Sec. 2.2 and Sec. 3.1).
+ * Errors: -EINVAL, -ERANGE, -ENOTRECOVERABLE, -ENOMEM, -EIO.
+ */
+int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
+                   uint32_t erasure_mask, uint64_t *d_img, int64_t S,
+                   mojette_stream_t stream);
+
+/*
+ * mojette_schedule -- the cached reconstruction path for one erasure mask,
+ * copied out for inspection (host only, touches no device).
+ *   survivors[Q]  receives the projection index dedicated to the left-to-
+ *                 right front of each line l (ascending p), then
+ *   survivors2[Q] the index dedicated to its right-to-left front;
+ *   split[Q]      pixel x of line l comes from the left front iff x < split[l];
+ *   steps         receives up to max_steps step words; bit 2l of word t set:
+ *                 line l's left front rebuilds its next pixel at step t,
+ *                 bit 2l+1: its right front does;
+ *   n_steps       receives the number of steps.
+ * Any output pointer may be NULL. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
+ */
+int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask,
+                     int32_t *survivors, int32_t *survivors2, int32_t *split,
+                     uint32_t *steps, int64_t max_steps, int64_t *n_steps);
+
+/*
+ * mojette_device_status -- synchronise the current device and return the
+ * sticky status word the kernels set (0 = clean; bit 0: a bounded wait for
+ * an asynchronous copy expired, so some outputs were not written).
+ *   flags  receives the word (may be NULL);
+ *   clear  nonzero: reset the word to 0 afterwards.
+ * Returns 0, -ETIMEDOUT if bit 0 was set, or -EIO.
+ */
+int mojette_device_status(uint32_t *flags, int clear);
+
+/* Text for a status code returned by any call above. */
+const char *mojette_strerror(int status);
+
+/* The last CUDA runtime error code seen by this library on this host thread
+ * (a cudaError_t value; 0 = none). */
+int mojette_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOJETTE_H */

@@ -1,0 +1,196 @@
+"""Thin ctypes binding over libmojette.so (C ABI: include/mojette.h).
+
+Argument marshalling only: every step of encode and decode runs in the CUDA
+library. Functions keep the C names. Device buffers may be given as torch
+tensors (8-byte elements, on the current CUDA device; ``data_ptr()`` is
+passed) or as raw integer device addresses. ``stream`` defaults to torch's
+current stream on the current device.
+
+Loading builds the library in-tree with nvcc when it is missing or stale and
+raises if that fails: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import errno
+import os
+import re
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+_U32 = ctypes.c_uint32
+_PTR = ctypes.c_void_p
+
+HEADER = os.path.join(_build.ROOT, "include", "mojette.h")
+
+
+class MojetteError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        self.code = code
+        name = errno.errorcode.get(-code, str(code))
+        super().__init__(f"{what}: {msg} ({name})")
+
+
+def lib():
+    """The loaded library (built on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            L.mojette_plan.argtypes = [_INT, _INT, _PTR, _INT, ctypes.POINTER(_PTR)]
+            L.mojette_plan_destroy.argtypes = [_PTR]
+            L.mojette_plan_info.argtypes = [_PTR, _PTR, _PTR, _PTR]
+            L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
+            L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
+            L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
+            L.mojette_device_status.argtypes = [ctypes.POINTER(_U32), _INT]
+            L.mojette_strerror.argtypes = [_INT]
+            L.mojette_strerror.restype = ctypes.c_char_p
+            L.mojette_last_cuda_error.argtypes = []
+            for name in ("mojette_plan", "mojette_plan_destroy", "mojette_plan_info",
+                         "mojette_encode", "mojette_decode", "mojette_schedule",
+                         "mojette_device_status", "mojette_last_cuda_error"):
+                getattr(L, name).restype = _INT
+            _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions include/mojette.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:int|const char \*|void)\s*\*?\s*(mojette_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+def mojette_strerror(code: int) -> str:
+    return lib().mojette_strerror(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        msg = mojette_strerror(code)
+        if code == -errno.EIO:
+            msg += f" [cudaError {lib().mojette_last_cuda_error()}]"
+        raise MojetteError(code, what, msg)
+
+
+def _addr(buf) -> int:
+    if buf is None:
+        return 0
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        if buf.element_size() != 8:
+            raise TypeError("buffers hold 64-bit words (torch.int64 or torch.uint64)")
+        if not buf.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return buf.data_ptr()
+    raise TypeError(f"cannot take a device address of {type(buf).__name__}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """Owns a ``mojette_plan_t``; geometry (P, Q, p) and its bin layout."""
+
+    def __init__(self, P: int, Q: int, p):
+        self.P, self.Q, self.p = int(P), int(Q), [int(v) for v in p]
+        arr = (ctypes.c_int * len(self.p))(*self.p)
+        h = _PTR()
+        _check(lib().mojette_plan(self.P, self.Q, arr, len(self.p), ctypes.byref(h)), "mojette_plan")
+        self.handle = h.value
+        self._lib = lib()
+        self.bins, self.offsets, self.total = mojette_plan_info(self)
+
+    @property
+    def n(self) -> int:
+        return len(self.p)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.mojette_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mojette_plan(P: int, Q: int, p) -> Plan:
+    return Plan(P, Q, p)
+
+
+def mojette_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def mojette_plan_info(plan: Plan):
+    n = len(plan.p)
+    bins = (_I64 * n)()
+    offs = (_I64 * n)()
+    total = _I64()
+    _check(lib().mojette_plan_info(plan.handle, bins, offs, ctypes.byref(total)), "mojette_plan_info")
+    return list(bins), list(offs), int(total.value)
+
+
+def mojette_encode(plan: Plan, d_img, d_proj, S: int | None = None, stream=None) -> None:
+    """Encode S stripes: d_img [S][Q][P] -> d_proj [S][total] (64-bit words)."""
+    if S is None:
+        S = d_img.numel() // (plan.P * plan.Q)
+    _check(lib().mojette_encode(plan.handle, _addr(d_img), _addr(d_proj), int(S), _stream(stream)),
+           "mojette_encode")
+
+
+def mojette_decode(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None = None,
+                   stream=None) -> None:
+    """Decode S stripes that lost the projections set in erasure_mask."""
+    if S is None:
+        S = d_img.numel() // (plan.P * plan.Q)
+    _check(lib().mojette_decode(plan.handle, _addr(d_proj), int(erasure_mask) & 0xFFFFFFFF,
+                                _addr(d_img), int(S), _stream(stream)), "mojette_decode")
+
+
+def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:
+    """The cached reconstruction path for one mask (host data)."""
+    Q = plan.Q
+    nsteps = _I64()
+    _check(lib().mojette_schedule(plan.handle, int(erasure_mask) & 0xFFFFFFFF, None, None, None,
+                                  None, 0, ctypes.byref(nsteps)), "mojette_schedule")
+    T = int(nsteps.value)
+    left = (ctypes.c_int32 * Q)()
+    right = (ctypes.c_int32 * Q)()
+    split = (ctypes.c_int32 * Q)()
+    steps = (ctypes.c_uint32 * max(T, 1))()
+    _check(lib().mojette_schedule(plan.handle, int(erasure_mask) & 0xFFFFFFFF, left, right, split,
+                                  steps, T, ctypes.byref(nsteps)), "mojette_schedule")
+    return {"left": list(left), "right": list(right), "split": list(split),
+            "steps": list(steps)[:T], "T": T}
+
+
+def mojette_device_status(clear: bool = True) -> int:
+    """Synchronise and return the device status word (raises on a timeout bit)."""
+    flags = _U32()
+    code = lib().mojette_device_status(ctypes.byref(flags), 1 if clear else 0)
+    _check(code, "mojette_device_status")
+    return int(flags.value)
+
+
+def mojette_last_cuda_error() -> int:
+    return int(lib().mojette_last_cuda_error())

@@ -1,0 +1,224 @@
+// extern "C" entry points of libmojette (declared in include/mojette.h).
+#include <cerrno>
+#include <cstring>
+#include <new>
+
+#include "mojette_internal.h"
+
+namespace mojette {
+
+// Sticky status word the kernels OR their error bits into (one per device:
+// a __device__ variable exists once in every context that loads the library).
+__device__ uint32_t g_status;
+
+namespace {
+thread_local int t_last_cuda = 0;
+std::mutex g_status_mu;
+std::map<int, uint32_t *> g_status_ptr;
+}  // namespace
+
+int record_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return 0;
+    t_last_cuda = (int)e;
+    return -EIO;
+}
+
+uint32_t *device_status_ptr(int *err)
+{
+    int device = 0;
+    if ((*err = record_cuda(cudaGetDevice(&device)))) return nullptr;
+    std::lock_guard<std::mutex> g(g_status_mu);
+    auto it = g_status_ptr.find(device);
+    if (it != g_status_ptr.end()) return it->second;
+    void *p = nullptr;
+    if ((*err = record_cuda(cudaGetSymbolAddress(&p, g_status)))) return nullptr;
+    g_status_ptr[device] = (uint32_t *)p;
+    return (uint32_t *)p;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace mojette
+
+using namespace mojette;
+
+extern "C" {
+
+int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out)
+{
+    if (!out || !p) return -EINVAL;
+    *out = nullptr;
+    if (P < 1 || Q < 1 || n < 1 || n > kMaxProj) return -EINVAL;
+    // keep every index of a stripe (and every bin offset) within int32
+    if ((int64_t)P * Q > (1 << 26)) return -EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (p[i] > (1 << 20) || p[i] < -(1 << 20)) return -EINVAL;
+        for (int k = i + 1; k < n; ++k)
+            if (p[i] == p[k]) return -EINVAL;
+    }
+    Plan *pl = new (std::nothrow) Plan();
+    if (!pl) return -ENOMEM;
+    pl->P = P;
+    pl->Q = Q;
+    pl->n = n;
+    int64_t t = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t ap = p[i] < 0 ? -(int64_t)p[i] : p[i];
+        pl->p[i] = p[i];
+        pl->B[i] = ap * (Q - 1) + P;                           // Eq. 2, q = 1
+        pl->bmin[i] = -(int64_t)(P - 1) + (p[i] < 0 ? (int64_t)(Q - 1) * p[i] : 0);
+        pl->off[i] = t;
+        t += pl->B[i];
+    }
+    if (t > (int64_t)1 << 30) {
+        delete pl;
+        return -EINVAL;
+    }
+    pl->total = t;
+    *out = reinterpret_cast<mojette_plan_t>(pl);
+    return 0;
+}
+
+int mojette_plan_destroy(mojette_plan_t plan)
+{
+    if (!plan) return 0;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    int cur = 0;
+    const bool have_device = cudaGetDevice(&cur) == cudaSuccess;
+    for (auto &kv : pl->schedules)
+        for (auto &d : kv.second->dev) {
+            if (have_device && cudaSetDevice(d.first) == cudaSuccess) cudaFree(d.second);
+        }
+    if (have_device) cudaSetDevice(cur);
+    delete pl;
+    return 0;
+}
+
+int mojette_plan_info(mojette_plan_t plan, int64_t *bins, int64_t *offsets, int64_t *total)
+{
+    if (!plan) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    for (int i = 0; i < pl->n; ++i) {
+        if (bins) bins[i] = pl->B[i];
+        if (offsets) offsets[i] = pl->off[i];
+    }
+    if (total) *total = pl->total;
+    return 0;
+}
+
+int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
+                   int64_t S, mojette_stream_t stream)
+{
+    if (!plan || S < 0) return -EINVAL;
+    if (S == 0) return 0;
+    if (!d_img || !d_proj) return -EINVAL;
+    if (!aligned16(d_img) || !aligned16(d_proj)) return -ERANGE;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    int err = 0;
+    EncodeArgs a;
+    a.img = d_img;
+    a.proj = d_proj;
+    a.S = S;
+    a.total = pl->total;
+    a.P = pl->P;
+    a.Q = pl->Q;
+    a.n = pl->n;
+    for (int i = 0; i < pl->n; ++i) {
+        a.p[i] = pl->p[i];
+        a.off[i] = pl->off[i];
+        a.bmin[i] = pl->bmin[i];
+    }
+    a.status = device_status_ptr(&err);
+    if (err) return err;
+    return launch_encode(a, (cudaStream_t)stream);
+}
+
+int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure_mask,
+                   uint64_t *d_img, int64_t S, mojette_stream_t stream)
+{
+    if (!plan || S < 0) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->Q > kMaxLines) return -EINVAL;
+    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;   // bits beyond n
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    if (S == 0) return 0;
+    if (!d_img || !d_proj) return -EINVAL;
+    if (!aligned16(d_img) || !aligned16(d_proj)) return -ERANGE;
+    uint32_t *dsteps = nullptr;
+    if ((err = schedule_on_device(*pl, *sc, &dsteps))) return err;
+    DecodeArgs a;
+    a.proj = d_proj;
+    a.img = d_img;
+    a.S = S;
+    a.total = pl->total;
+    a.P = pl->P;
+    a.Q = pl->Q;
+    a.T = sc->T;
+    a.steps = dsteps;
+    for (int l = 0; l < pl->Q; ++l) {
+        a.pL[l] = sc->pL[l];
+        a.pR[l] = sc->pR[l];
+        a.split[l] = sc->split[l];
+        a.srcL[l] = sc->srcL[l];
+        a.srcR[l] = sc->srcR[l];
+    }
+    a.status = device_status_ptr(&err);
+    if (err) return err;
+    return launch_decode(a, (cudaStream_t)stream);
+}
+
+int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *survivors,
+                     int32_t *survivors2, int32_t *split, uint32_t *steps,
+                     int64_t max_steps, int64_t *n_steps)
+{
+    if (!plan) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->Q > kMaxLines) return -EINVAL;
+    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    for (int l = 0; l < pl->Q; ++l) {
+        if (survivors) survivors[l] = sc->projL[l];
+        if (survivors2) survivors2[l] = sc->projR[l];
+        if (split) split[l] = sc->split[l];
+    }
+    if (steps)
+        for (int64_t t = 0; t < sc->T && t < max_steps; ++t) steps[t] = sc->steps[(size_t)t];
+    if (n_steps) *n_steps = sc->T;
+    return 0;
+}
+
+int mojette_device_status(uint32_t *flags, int clear)
+{
+    int err = 0;
+    uint32_t *d = device_status_ptr(&err);
+    if (!d) return err;
+    if ((err = record_cuda(cudaDeviceSynchronize()))) return err;
+    uint32_t h = 0;
+    if ((err = record_cuda(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost)))) return err;
+    if (clear && (err = record_cuda(cudaMemset(d, 0, sizeof(h))))) return err;
+    if (flags) *flags = h;
+    return (h & kStatusWaitTimeout) ? -ETIMEDOUT : 0;
+}
+
+const char *mojette_strerror(int status)
+{
+    switch (status) {
+    case 0: return "success";
+    case -EINVAL: return "invalid argument or geometry";
+    case -ERANGE: return "device pointer not 16-byte aligned";
+    case -ENOTRECOVERABLE: return "surviving projections cannot rebuild the image";
+    case -ENOMEM: return "out of memory";
+    case -EIO: return "CUDA runtime error (see mojette_last_cuda_error)";
+    case -ETIMEDOUT: return "a bounded device-side wait expired";
+    default: return "unknown status";
+    }
+}
+
+int mojette_last_cuda_error(void) { return t_last_cuda; }
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// Host side of libmojette: reconstruction schedules and their cache.
+//
+// Sec. 2.2 of the paper: reconstruction propagates from the image corners
+// inward, and when one projection is dedicated to each line the
+// reconstruction path can be fixed in advance (Normand et al., DGCI 2006).
+// With directions (p, 1) this works as follows. Sort the Q projections used
+// by p, ascending; line l takes the l-th one, p_(l). A pixel (l, x) is
+// rebuilt from the bin b = l p_(l) - x of that projection: the bin's value
+// XOR the other pixels of its discrete line, (l', x + (l' - l) p_(l)) for
+// l' != l, that lie inside the image. Sweeping every line from left to
+// right, those other pixels are already known once the lines are staggered
+// suitably, because p_(l) increases with l. The mirror image of the same
+// argument (directions -p) gives a right-to-left sweep in which line l takes
+// the l-th largest p. Running both sweeps at once halves the number of
+// sequential steps; the point where they meet on each line is where the
+// greedy step-by-step simulation below finds them.
+//
+// A schedule records, for every step, which line fronts advance; the device
+// replays it for every stripe that lost the same projections. Building it is
+// the paper's excluded pre-computation (Sec. 3.1).
+#include <algorithm>
+#include <cerrno>
+#include <cstring>
+#include <numeric>
+
+#include "mojette_internal.h"
+
+namespace mojette {
+
+namespace {
+
+// Left/right two-front sweep for one choice of Q projections (indices into
+// the plan, sorted by ascending direction). Fills `out` and returns the
+// number of steps, or -1 if the sweep stalls or exceeds `limit` steps.
+int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
+{
+    const int P = pl.P, Q = pl.Q;
+    int32_t pL[kMaxLines], pR[kMaxLines];
+    for (int l = 0; l < Q; ++l) {
+        pL[l] = pl.p[asc[l]];
+        pR[l] = pl.p[asc[Q - 1 - l]];
+    }
+    std::vector<uint8_t> known((size_t)P * Q, 0);
+    int a[kMaxLines], z[kMaxLines];
+    for (int l = 0; l < Q; ++l) { a[l] = 0; z[l] = P - 1; }
+    int64_t remaining = (int64_t)P * Q;
+    std::vector<uint32_t> steps;
+
+    // pixel (l, x) rebuilt along direction p: every other in-image pixel of
+    // its line must be known before this step
+    auto ready = [&](int l, int x, int p) {
+        for (int l2 = 0; l2 < Q; ++l2) {
+            if (l2 == l) continue;
+            const int64_t x2 = (int64_t)x + (int64_t)(l2 - l) * p;
+            if (x2 < 0 || x2 >= P) continue;
+            if (!known[(size_t)l2 * P + x2]) return false;
+        }
+        return true;
+    };
+
+    while (remaining > 0) {
+        if ((int)steps.size() >= limit) return -1;
+        uint32_t word = 0;
+        for (int l = 0; l < Q; ++l) {
+            if (a[l] > z[l]) continue;
+            bool left = ready(l, a[l], pL[l]);
+            if (left) word |= 1u << (2 * l);
+            if ((!left || a[l] < z[l]) && ready(l, z[l], pR[l])) word |= 2u << (2 * l);
+        }
+        if (!word) return -1;
+        for (int l = 0; l < Q; ++l) {
+            const uint32_t bits = word >> (2 * l) & 3u;
+            if (bits & 1u) { known[(size_t)l * P + a[l]] = 1; ++a[l]; --remaining; }
+            if (bits & 2u) { known[(size_t)l * P + z[l]] = 1; --z[l]; --remaining; }
+        }
+        steps.push_back(word);
+    }
+    if (out) {
+        out->T = (int)steps.size();
+        out->steps = std::move(steps);
+        for (int l = 0; l < Q; ++l) {
+            const int iL = asc[l], iR = asc[Q - 1 - l];
+            out->projL[l] = iL;
+            out->projR[l] = iR;
+            out->pL[l] = pl.p[iL];
+            out->pR[l] = pl.p[iR];
+            out->split[l] = a[l];
+            // bin j = l p - x - b_min at word off + j of the stripe block
+            out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
+            out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
+        }
+    }
+    return out ? out->T : (int)steps.size();
+}
+
+// Cap on the number of Q-subsets of the survivors tried per mask.
+constexpr int kMaxCandidates = 512;
+
+}  // namespace
+
+int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
+{
+    if (pl.Q > kMaxLines) return -EINVAL;
+    std::vector<int> surv;
+    for (int i = 0; i < pl.n; ++i)
+        if (!(mask >> i & 1u)) surv.push_back(i);
+    if ((int)surv.size() < pl.Q) return -ENOTRECOVERABLE;
+
+    // Any Q survivors rebuild the same image (Eq. 3 gives uniqueness); pick
+    // the subset with the fewest steps. Candidates are enumerated with the
+    // smallest |p| first.
+    std::stable_sort(surv.begin(), surv.end(), [&](int x, int y) {
+        const int ax = pl.p[x] < 0 ? -pl.p[x] : pl.p[x];
+        const int ay = pl.p[y] < 0 ? -pl.p[y] : pl.p[y];
+        return ax < ay;
+    });
+    const int m = (int)surv.size(), Q = pl.Q;
+    std::vector<int> pick(Q);
+    std::iota(pick.begin(), pick.end(), 0);
+    int best = -1;
+    Schedule tmp;
+    int tried = 0;
+    while (true) {
+        std::vector<int> asc(Q);
+        for (int k = 0; k < Q; ++k) asc[k] = surv[pick[k]];
+        std::sort(asc.begin(), asc.end(), [&](int x, int y) { return pl.p[x] < pl.p[y]; });
+        const int limit = best < 0 ? (1 << 30) : best;
+        const int T = sweep(pl, asc, limit, &tmp);
+        if (T >= 0 && (best < 0 || T < best)) {
+            best = T;
+            *out = tmp;
+        }
+        if (++tried >= kMaxCandidates) break;
+        // next combination of Q out of m
+        int k = Q - 1;
+        while (k >= 0 && pick[k] == m - Q + k) --k;
+        if (k < 0) break;
+        ++pick[k];
+        for (int r = k + 1; r < Q; ++r) pick[r] = pick[r - 1] + 1;
+    }
+    if (best < 0) return -ENOTRECOVERABLE;
+    out->mask = mask;
+    out->dev.clear();
+    return 0;
+}
+
+Schedule *get_schedule(Plan &pl, uint32_t mask, int *err)
+{
+    std::lock_guard<std::mutex> g(pl.mu);
+    auto it = pl.schedules.find(mask);
+    if (it != pl.schedules.end()) return it->second.get();
+    std::unique_ptr<Schedule> sc;
+    try {
+        sc.reset(new Schedule());
+    } catch (...) {
+        *err = -ENOMEM;
+        return nullptr;
+    }
+    const int r = build_schedule(pl, mask, sc.get());
+    if (r) {
+        *err = r;
+        return nullptr;
+    }
+    Schedule *raw = sc.get();
+    pl.schedules[mask] = std::move(sc);
+    return raw;
+}
+
+int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev)
+{
+    int device = 0;
+    int r = record_cuda(cudaGetDevice(&device));
+    if (r) return r;
+    std::lock_guard<std::mutex> g(pl.mu);
+    auto it = sc.dev.find(device);
+    if (it != sc.dev.end()) {
+        *dev = it->second;
+        return 0;
+    }
+    uint32_t *d = nullptr;
+    const size_t bytes = std::max<size_t>(4, sc.steps.size() * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        record_cuda(e);
+        return -ENOMEM;
+    }
+    if ((r = record_cuda(e))) return r;
+    if ((r = record_cuda(cudaMemcpy(d, sc.steps.data(), sc.steps.size() * sizeof(uint32_t),
+                                    cudaMemcpyHostToDevice)))) {
+        cudaFree(d);
+        return r;
+    }
+    sc.dev[device] = d;
+    *dev = d;
+    return 0;
+}
+
+}  // namespace mojette

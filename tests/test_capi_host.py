@@ -1,0 +1,146 @@
+"""Host-side checks of libmojette that need no GPU.
+
+The library must load and export every function include/mojette.h declares;
+plans must have the layout of Eq. 2; and every reconstruction schedule the
+library builds must be a valid path -- replayed here on the CPU, step by
+step, with the gather rule of Sec. 2.2 on bins from the oracle's encoder, it
+must rebuild the oracle's image exactly.
+"""
+import ctypes
+import errno
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_07038_gb300 import binding as mj
+from paper_1504_07038_gb300 import inputs
+
+CONFIGS = [
+    (128, 4, [-3, -2, -1, 1, 2, 3]),
+    (256, 4, [-3, -2, -1, 1, 2, 3]),
+    (64, 8, [v for v in range(-6, 7) if v]),
+    (128, 8, [v for v in range(-6, 7) if v]),
+    (256, 2, [-1, 1, 2]),
+]
+
+
+def test_library_exports_every_header_function():
+    names = mj.header_functions()
+    assert {"mojette_plan", "mojette_encode", "mojette_decode", "mojette_plan_destroy",
+            "mojette_plan_info", "mojette_schedule", "mojette_device_status",
+            "mojette_strerror", "mojette_last_cuda_error"} <= set(names)
+    L = mj.lib()
+    for n in names:
+        assert hasattr(L, n), n
+        assert ctypes.cast(getattr(L, n), ctypes.c_void_p).value
+
+
+@pytest.mark.parametrize("P,Q,p", CONFIGS + [(5, 3, [0, 7, -9]), (1, 1, [4])])
+def test_plan_layout_matches_eq2(P, Q, p):
+    plan = mj.mojette_plan(P, Q, p)
+    off, bins, _, total = oracle.offsets(p, P, Q)
+    assert plan.bins == bins and plan.offsets == off and plan.total == total
+
+
+@pytest.mark.parametrize("args", [
+    (0, 4, [1]), (8, 0, [1]), (8, 4, []), (8, 4, [1, 1]), (8, 4, list(range(33))),
+])
+def test_plan_rejects_bad_geometry(args):
+    with pytest.raises(mj.MojetteError) as e:
+        mj.mojette_plan(*args)
+    assert e.value.code == -errno.EINVAL
+
+
+def test_calls_validate_arguments_without_a_device():
+    plan = mj.mojette_plan(16, 4, [-2, -1, 1, 2])
+    L = mj.lib()
+    assert L.mojette_encode(None, 16, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_encode(plan.handle, 16, 16, -1, None) == -errno.EINVAL
+    assert L.mojette_encode(plan.handle, 0, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_encode(plan.handle, 8, 16, 1, None) == -errno.ERANGE
+    assert L.mojette_encode(plan.handle, 16, 16, 0, None) == 0          # S = 0: no-op
+    assert L.mojette_decode(plan.handle, 16, 1 << 5, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_decode(plan.handle, 16, 0b0111, 16, 1, None) == -errno.ENOTRECOVERABLE
+    assert L.mojette_decode(plan.handle, 16, 0, 24, 1, None) == -errno.ERANGE
+    assert mj.mojette_strerror(-errno.ENOTRECOVERABLE).startswith("surviving")
+
+
+def replay(sched, plan, proj, P, Q, p):
+    """Run a schedule on the CPU for all stripes at once; check it is a
+    valid path (each pixel once, every other pixel of its line known at an
+    earlier step) and return the image."""
+    S = proj.shape[0]
+    img = np.zeros((S, Q, P), dtype=np.uint64)
+    step_of = np.full((Q, P), -1)
+    left, right, split = sched["left"], sched["right"], sched["split"]
+    xa, xz = [0] * Q, [P - 1] * Q
+    for t, w in enumerate(sched["steps"]):
+        done = []
+        for l in range(Q):
+            for side in (0, 1):
+                if not (w >> (2 * l + side) & 1):
+                    continue
+                x = xa[l] if side == 0 else xz[l]
+                i = left[l] if side == 0 else right[l]
+                assert (x < split[l]) == (side == 0)
+                assert step_of[l, x] < 0
+                pi = p[i]
+                bmin = -(P - 1) + min(0, (Q - 1) * pi)
+                v = proj[:, plan.offsets[i] + (l * pi - x - bmin)].copy()
+                for l2 in range(Q):
+                    x2 = x + (l2 - l) * pi
+                    if l2 == l or not 0 <= x2 < P:
+                        continue
+                    assert 0 <= step_of[l2, x2] < t, (l, x, l2, x2)
+                    v ^= img[:, l2, x2]
+                done.append((l, x, v))
+                if side == 0:
+                    xa[l] += 1
+                else:
+                    xz[l] -= 1
+        for l, x, v in done:
+            img[:, l, x] = v
+            step_of[l, x] = t
+    assert (step_of >= 0).all()
+    return img
+
+
+@pytest.mark.parametrize("P,Q,p", CONFIGS)
+def test_schedules_replay_to_the_oracle_image(P, Q, p):
+    n = len(p)
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(3, Q, P, seed=11)
+    proj = oracle.encode(img, p)
+    masks = []
+    for e in range(0, n - Q + 1):
+        ms = inputs.all_masks(n, e)
+        masks += ms if len(ms) <= 40 else ms[:: len(ms) // 40]
+    for m in masks:
+        sched = mj.mojette_schedule(plan, m)
+        used = set(sched["left"]) | set(sched["right"])
+        assert all(not (m >> i & 1) for i in used)          # erased projections never read
+        assert len(set(sched["left"])) == Q
+        assert [p[i] for i in sched["left"]] == sorted(p[i] for i in sched["left"])
+        assert sched["T"] <= P + 2 * Q * max(abs(v) for v in p)   # about P/2 steps per front
+        assert (replay(sched, plan, proj, P, Q, p) == img).all(), m
+
+
+def test_schedule_for_every_small_geometry():
+    """Exhaustive over tiny geometries: every k-of-n mask yields a path that
+    rebuilds the image (Eq. 3 says it exists; c9 of the design checks the
+    sweep never stalls)."""
+    rng = np.random.default_rng(5)
+    for P in range(1, 9):
+        for Q in range(1, 5):
+            for _ in range(2):
+                n = int(rng.integers(Q, Q + 3))
+                p = sorted(rng.choice(np.arange(-5, 6), size=n, replace=False).tolist())
+                plan = mj.mojette_plan(P, Q, p)
+                img = inputs.stripes(2, Q, P, seed=P * 10 + Q)
+                proj = oracle.encode(img, p)
+                for m in range(1 << n):
+                    if n - bin(m).count("1") < Q:
+                        continue
+                    sched = mj.mojette_schedule(plan, m)
+                    assert (replay(sched, plan, proj, P, Q, p) == img).all(), (P, Q, p, m)

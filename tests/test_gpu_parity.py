@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit-exact.
+
+Encode and decode run through the C ABI (ctypes binding) on cuda:0 and are
+compared element by element with the oracle on the same seeded inputs: at
+sizes spanning many tiles with ragged tails, on every erasure pattern of the
+benchmark geometries, on edge cases (tiny, odd-sized and degenerate
+geometries), and at the full benchmark sizes on sampled stripes plus the
+size-independent property decode(encode(img)) == img on every stripe.
+Integer XOR work: the tolerance is zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_07038_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_1504_07038_gb300 import binding as mj
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def host(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def empty(shape, fill=0x5A5A5A5A5A5A5A5A):
+    t = torch.empty(shape, dtype=torch.int64, device="cuda")
+    t.fill_(fill - (1 << 64) if fill >= (1 << 63) else fill)
+    return t
+
+
+@pytest.fixture(autouse=True)
+def clean_status():
+    mj.mojette_device_status(clear=True)
+    yield
+    assert mj.mojette_device_status(clear=True) == 0
+
+
+SIX = [-3, -2, -1, 1, 2, 3]
+TWELVE = [v for v in range(-6, 7) if v]
+GEOMS = [
+    ("4KB(6,4)", 128, 4, SIX),
+    ("8KB(6,4)", 256, 4, SIX),
+    ("4KB(12,8)", 64, 8, TWELVE),
+    ("8KB(12,8)", 128, 8, TWELVE),
+    ("4KB(3,2)", 256, 2, [-1, 1, 2]),
+    ("8KB(3,2)", 512, 2, [-1, 1, 2]),
+]
+
+
+def encode_gpu(plan, img_np):
+    S = img_np.shape[0]
+    out = empty((S, plan.total))
+    mj.mojette_encode(plan, dev(img_np), out, S)
+    torch.cuda.synchronize()
+    return host(out)
+
+
+def decode_gpu(plan, proj_np, mask, S=None):
+    S = proj_np.shape[0] if S is None else S
+    out = empty((S, plan.Q, plan.P))
+    mj.mojette_decode(plan, dev(proj_np), mask, out, S)
+    torch.cuda.synchronize()
+    return host(out)
+
+
+@pytest.mark.parametrize("name,P,Q,p", GEOMS)
+@pytest.mark.parametrize("S", [1, 7, 1023, 1024])
+def test_encode_matches_oracle(name, P, Q, p, S):
+    img = inputs.stripes(S, Q, P, seed=S + P)
+    plan = mj.mojette_plan(P, Q, p)
+    assert (encode_gpu(plan, img) == oracle.encode(img, p, threads=8)).all()
+
+
+@pytest.mark.parametrize("name,P,Q,p", GEOMS)
+def test_decode_every_erasure_pattern(name, P, Q, p):
+    """Every mask with n - Q erasures (all 15 / 495 / 3), and samples of the
+    masks with fewer, decoded from oracle-made projections."""
+    n = len(p)
+    S = 67
+    img = inputs.stripes(S, Q, P, seed=3)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    d_proj = dev(proj)
+    masks = inputs.all_masks(n, n - Q)
+    for e in range(0, n - Q):
+        ms = inputs.all_masks(n, e)
+        masks += ms if len(ms) <= 24 else ms[:: len(ms) // 24]
+    out = empty((S, Q, P))
+    for m in masks:
+        out.fill_(0x1234)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        got = host(out)
+        assert (got == img).all(), (name, m)
+    # the last mask also against the oracle's own decoder
+    assert (host(out) == oracle.decode(proj, p, P, Q, masks[-1], threads=8)).all()
+
+
+@pytest.mark.parametrize("name,P,Q,p", GEOMS[:4])
+def test_round_trip_on_gpu_with_ragged_batches(name, P, Q, p):
+    for S in [1, 5, 33, 1000]:
+        img = inputs.stripes(S, Q, P, seed=S)
+        plan = mj.mojette_plan(P, Q, p)
+        d_img = dev(img)
+        d_proj = empty((S, plan.total))
+        mj.mojette_encode(plan, d_img, d_proj, S)
+        mask = int(inputs.erasure_masks(1, len(p), len(p) - Q, seed=S)[0])
+        out = empty((S, Q, P))
+        mj.mojette_decode(plan, d_proj, mask, out, S)
+        torch.cuda.synchronize()
+        assert (host(out) == img).all()
+
+
+def _tiny():
+    rng = np.random.default_rng(77)
+    cases = []
+    for P in [1, 2, 3, 5, 8, 13]:
+        for Q in [1, 2, 3, 4, 5, 16]:
+            n = int(min(Q + int(rng.integers(0, 3)), 11))
+            p = sorted(rng.choice(np.arange(-5, 6), size=n, replace=False).tolist())
+            cases.append((P, Q, p))
+    cases.append((9, 16, list(range(-9, 0)) + list(range(1, 9))))   # Q = 16, n = 17
+    return cases
+
+
+@pytest.mark.parametrize("P,Q,p", _tiny())
+def test_edge_geometries(P, Q, p):
+    """Tiny and odd geometries: Q*P odd (non-bulk staging), |p| > P (empty
+    bins), p = 0, Q = 1, Q not a power of two, Q = 16 (largest decode)."""
+    S = 45
+    img = inputs.stripes(S, Q, P, seed=P * 31 + Q)
+    plan = mj.mojette_plan(P, Q, p)
+    proj = oracle.encode(img, p)
+    assert (encode_gpu(plan, img) == proj).all()
+    n = len(p)
+    for e in range(0, n - Q + 1):
+        for m in inputs.all_masks(n, e)[:6]:
+            assert (decode_gpu(plan, proj, m) == img).all(), (P, Q, p, m)
+
+
+def test_output_bounds_untouched():
+    """Nothing is written outside [0, S) stripes (canaries on both sides)."""
+    P, Q, p = 128, 8, TWELVE
+    S = 301
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(S, Q, P)
+    pad = 64
+    proj_buf = empty((S * plan.total + 2 * pad,), fill=0x0F0F)
+    mj.mojette_encode(plan, dev(img), proj_buf[pad:pad + S * plan.total], S)
+    h = host(proj_buf)
+    assert (h[:pad] == 0x0F0F).all() and (h[-pad:] == 0x0F0F).all()
+    assert (h[pad:-pad].reshape(S, -1) == oracle.encode(img, p, threads=8)).all()
+    img_buf = empty((S * Q * P + 2 * pad,), fill=0x0F0F)
+    mj.mojette_decode(plan, proj_buf[pad:pad + S * plan.total], 0b111100000000,
+                      img_buf[pad:pad + S * Q * P], S)
+    h = host(img_buf)
+    assert (h[:pad] == 0x0F0F).all() and (h[-pad:] == 0x0F0F).all()
+    assert (h[pad:-pad].reshape(S, Q, P) == img).all()
+
+
+def test_too_few_survivors_refused_before_launch():
+    plan = mj.mojette_plan(128, 4, SIX)
+    buf = empty((8, plan.total))
+    img = empty((8, 4, 128))
+    with pytest.raises(mj.MojetteError):
+        mj.mojette_decode(plan, buf, 0b000111, img, 8)
+
+
+def _full_size(P, Q, p, S, masks, sample=48):
+    """Full-size encode + decode in the benchmark's launch configuration:
+    sampled stripes against the oracle, every stripe against the input."""
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(S, Q, P)
+    d_img = dev(img)
+    d_proj = empty((S, plan.total))
+    mj.mojette_encode(plan, d_img, d_proj, S)
+    rng = np.random.default_rng(S)
+    idx = np.unique(np.concatenate([[0, S - 1], rng.integers(0, S, sample)]))
+    ref_img = inputs.stripe_rows(idx, Q, P)
+    ref_proj = oracle.encode(ref_img, p, threads=8)
+    got = host(d_proj[torch.from_numpy(idx).cuda()])
+    assert (got == ref_proj).all()
+    out = empty((S, Q, P))
+    for m in masks:
+        out.fill_(0)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        assert bool((out == d_img).all())
+        assert (host(out[torch.from_numpy(idx).cuda()]) ==
+                oracle.decode(ref_proj, p, P, Q, m, threads=8)).all()
+
+
+def test_full_size_plain_at_scale_every_two_erasure_mask():
+    """262144 stripes of 8 KB, (6,4): encode, then decode under all 15
+    two-erasure patterns."""
+    _full_size(256, 4, SIX, 262144, inputs.all_masks(6, 2))
+
+
+def test_full_size_wide_geometry():
+    """262144 stripes at 4 KB and 8 KB, (12,8), four erasures (a sample of the
+    495 patterns at full size; all 495 run at small size above)."""
+    ms = inputs.all_masks(12, 4)
+    _full_size(64, 8, TWELVE, 262144, ms[::61])
+    _full_size(128, 8, TWELVE, 262144, ms[7::83])
