@@ -119,13 +119,22 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
  *   split[Q]      pixel x of line l comes from the left front iff x < split[l];
  *   steps         receives up to max_steps step words; bit 2l of word t set:
  *                 line l's left front rebuilds its next pixel at step t,
- *                 bit 2l+1: its right front does;
+ *                 bit 2l+1: its right front does; for Q <= 15, bit 31 marks
+ *                 a steady step (every front moves, and every line's operand
+ *                 on line l+1 comes from the same step exactly where the
+ *                 schedule's steady pattern says so);
+ *   forward       receives up to max_steps words; bit 2l+side of word t set:
+ *                 at step t, line l of that front (0 left, 1 right) takes
+ *                 the pixel of its bin line on line l+1 from the pixel line
+ *                 l+1 of the same front rebuilds in the same step (fronts
+ *                 visit their lines from Q-1 down to 0 within a step);
  *   n_steps       receives the number of steps.
  * Any output pointer may be NULL. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
  */
 int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask,
                      int32_t *survivors, int32_t *survivors2, int32_t *split,
-                     uint32_t *steps, int64_t max_steps, int64_t *n_steps);
+                     uint32_t *steps, uint32_t *forward, int64_t max_steps,
+                     int64_t *n_steps);
 
 /*
  * mojette_device_status -- synchronise the current device and return the

@@ -49,7 +49,7 @@ def lib():
             L.mojette_plan_info.argtypes = [_PTR, _PTR, _PTR, _PTR]
             L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
-            L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
+            L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_device_status.argtypes = [ctypes.POINTER(_U32), _INT]
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
@@ -172,16 +172,17 @@ def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:
     Q = plan.Q
     nsteps = _I64()
     _check(lib().mojette_schedule(plan.handle, int(erasure_mask) & 0xFFFFFFFF, None, None, None,
-                                  None, 0, ctypes.byref(nsteps)), "mojette_schedule")
+                                  None, None, 0, ctypes.byref(nsteps)), "mojette_schedule")
     T = int(nsteps.value)
     left = (ctypes.c_int32 * Q)()
     right = (ctypes.c_int32 * Q)()
     split = (ctypes.c_int32 * Q)()
     steps = (ctypes.c_uint32 * max(T, 1))()
+    forward = (ctypes.c_uint32 * max(T, 1))()
     _check(lib().mojette_schedule(plan.handle, int(erasure_mask) & 0xFFFFFFFF, left, right, split,
-                                  steps, T, ctypes.byref(nsteps)), "mojette_schedule")
+                                  steps, forward, T, ctypes.byref(nsteps)), "mojette_schedule")
     return {"left": list(left), "right": list(right), "split": list(split),
-            "steps": list(steps)[:T], "T": T}
+            "steps": list(steps)[:T], "forward": list(forward)[:T], "T": T}
 
 
 def mojette_device_status(clear: bool = True) -> int:

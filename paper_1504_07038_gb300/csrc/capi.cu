@@ -158,6 +158,7 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     a.Q = pl->Q;
     a.T = sc->T;
     a.steps = dsteps;
+    a.fwd = sc->fwd;
     for (int l = 0; l < pl->Q; ++l) {
         a.pL[l] = sc->pL[l];
         a.pR[l] = sc->pR[l];
@@ -172,7 +173,7 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
 
 int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *survivors,
                      int32_t *survivors2, int32_t *split, uint32_t *steps,
-                     int64_t max_steps, int64_t *n_steps)
+                     uint32_t *forward, int64_t max_steps, int64_t *n_steps)
 {
     if (!plan) return -EINVAL;
     Plan *pl = reinterpret_cast<Plan *>(plan);
@@ -186,8 +187,10 @@ int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *surviv
         if (survivors2) survivors2[l] = sc->projR[l];
         if (split) split[l] = sc->split[l];
     }
-    if (steps)
-        for (int64_t t = 0; t < sc->T && t < max_steps; ++t) steps[t] = sc->steps[(size_t)t];
+    for (int64_t t = 0; t < sc->T && t < max_steps; ++t) {
+        if (steps) steps[t] = sc->steps[(size_t)t];
+        if (forward) forward[t] = sc->fwdw[(size_t)t];
+    }
     if (n_steps) *n_steps = sc->T;
     return 0;
 }

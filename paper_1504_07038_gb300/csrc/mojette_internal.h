@@ -19,6 +19,12 @@ constexpr int kMaxLines = MOJETTE_MAX_DECODE_LINES;
 // Status bits the kernels OR into the device status word.
 constexpr uint32_t kStatusWaitTimeout = 1u;
 
+// Step word bit 31 marks a steady step: every front moves and the operand
+// pattern is the schedule's `fwd` (see plan.cpp). Lines use bits 0..2Q-1, so
+// the mark exists for Q <= 15.
+constexpr uint32_t kStepSteady = 1u << 31;
+constexpr int kFastMaxLines = 15;
+
 // A bounded device-side wait gives up after this many nanoseconds.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -28,6 +34,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 struct Schedule {
     uint32_t mask = 0;
     int T = 0;                       // number of steps
+    uint32_t fwd = 0;                // operand pattern of the steady steps
     int32_t projL[kMaxLines] = {};   // projection rebuilding line l left of split
     int32_t projR[kMaxLines] = {};   // ... and from split rightwards
     int32_t pL[kMaxLines] = {};      // their directions
@@ -36,7 +43,9 @@ struct Schedule {
     int64_t srcL[kMaxLines] = {};    // bin of pixel (l, x) sits at word srcL[l] - x
     int64_t srcR[kMaxLines] = {};    //   of the stripe's projection block
     std::vector<uint32_t> steps;     // T words, 2 bits per line
-    std::map<int, uint32_t *> dev;   // device copy of `steps`, per device
+    std::vector<uint32_t> fwdw;      // T words: bit 2l+side set when line l of that
+                                     // front uses line l+1's pixel of the same step
+    std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
 };
 
 struct Plan {
@@ -81,6 +90,7 @@ struct DecodeArgs {
     int P, Q;
     int T;
     const uint32_t *steps;          // device
+    uint32_t fwd;                   // operand pattern of the steady steps
     int32_t pL[kMaxLines], pR[kMaxLines], split[kMaxLines];
     int64_t srcL[kMaxLines], srcR[kMaxLines];
     uint32_t *status;

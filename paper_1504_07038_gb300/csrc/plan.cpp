@@ -13,7 +13,10 @@
 // argument (directions -p) gives a right-to-left sweep in which line l takes
 // the l-th largest p. Running both sweeps at once halves the number of
 // sequential steps; the point where they meet on each line is where the
-// greedy step-by-step simulation below finds them.
+// greedy step-by-step simulation below finds them. Within a step a front
+// visits its lines from Q-1 down to 0, so that line l may use the pixel
+// line l + 1 rebuilt in the same step: the chain between lines with
+// neighbouring directions then costs no extra step.
 //
 // A schedule records, for every step, which line fronts advance; the device
 // replays it for every stripe that lost the same projections. Building it is
@@ -21,6 +24,7 @@
 #include <algorithm>
 #include <cerrno>
 #include <cstring>
+#include <map>
 #include <numeric>
 
 #include "mojette_internal.h"
@@ -30,67 +34,106 @@ namespace mojette {
 namespace {
 
 // Left/right two-front sweep for one choice of Q projections (indices into
-// the plan, sorted by ascending direction). Fills `out` and returns the
-// number of steps, or -1 if the sweep stalls or exceeds `limit` steps.
+// the plan, sorted by ascending direction). At every step each front visits
+// its lines from l = Q-1 down to 0 and rebuilds the next pixel of a line
+// when every other in-image pixel of the pixel's bin line is known: rebuilt
+// at an earlier step by either front, or -- for line l + 1 only -- by the
+// same front earlier in the same step (the device keeps that value in a
+// register). With the lines staggered by the dedicated directions this lets
+// every front move one column per step, so a sweep takes about P/2 steps.
+// Fills `out` and returns the number of steps, or -1 if the sweep stalls or
+// reaches `limit` steps.
 int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
 {
     const int P = pl.P, Q = pl.Q;
-    int32_t pL[kMaxLines], pR[kMaxLines];
+    int32_t pF[2][kMaxLines];
     for (int l = 0; l < Q; ++l) {
-        pL[l] = pl.p[asc[l]];
-        pR[l] = pl.p[asc[Q - 1 - l]];
+        pF[0][l] = pl.p[asc[l]];
+        pF[1][l] = pl.p[asc[Q - 1 - l]];
     }
     std::vector<uint8_t> known((size_t)P * Q, 0);
-    int a[kMaxLines], z[kMaxLines];
+    int a[kMaxLines], z[kMaxLines], took[2][kMaxLines];
     for (int l = 0; l < Q; ++l) { a[l] = 0; z[l] = P - 1; }
     int64_t remaining = (int64_t)P * Q;
-    std::vector<uint32_t> steps;
-
-    // pixel (l, x) rebuilt along direction p: every other in-image pixel of
-    // its line must be known before this step
-    auto ready = [&](int l, int x, int p) {
-        for (int l2 = 0; l2 < Q; ++l2) {
-            if (l2 == l) continue;
-            const int64_t x2 = (int64_t)x + (int64_t)(l2 - l) * p;
-            if (x2 < 0 || x2 >= P) continue;
-            if (!known[(size_t)l2 * P + x2]) return false;
-        }
-        return true;
-    };
+    std::vector<uint32_t> steps, pattern;
 
     while (remaining > 0) {
         if ((int)steps.size() >= limit) return -1;
         uint32_t word = 0;
-        for (int l = 0; l < Q; ++l) {
-            if (a[l] > z[l]) continue;
-            bool left = ready(l, a[l], pL[l]);
-            if (left) word |= 1u << (2 * l);
-            if ((!left || a[l] < z[l]) && ready(l, z[l], pR[l])) word |= 2u << (2 * l);
+        for (int side = 0; side < 2; ++side) {
+            for (int l = Q - 1; l >= 0; --l) {
+                took[side][l] = -1;
+                if (a[l] > z[l]) continue;
+                const int x = side ? z[l] : a[l];
+                if (side == 1 && took[0][l] == x) continue;   // the fronts met on this pixel
+                const int p = pF[side][l];
+                bool ready = true;
+                for (int l2 = 0; l2 < Q && ready; ++l2) {
+                    if (l2 == l) continue;
+                    const int64_t x2 = (int64_t)x + (int64_t)(l2 - l) * p;
+                    if (x2 < 0 || x2 >= P) continue;
+                    if (known[(size_t)l2 * P + x2]) continue;
+                    if (l2 == l + 1 && took[side][l2] == x2) continue;
+                    ready = false;
+                }
+                if (ready) {
+                    took[side][l] = x;
+                    word |= 1u << (2 * l + side);
+                }
+            }
         }
         if (!word) return -1;
+        // Operand pattern of the step: bit 2l+side set when line l of that
+        // front takes its line l+1 operand from the pixel line l+1 rebuilt
+        // in this same step (otherwise the operand is an earlier pixel, or a
+        // pixel outside the image, and is read from memory).
+        uint32_t fwd = 0;
+        for (int side = 0; side < 2; ++side)
+            for (int l = 0; l + 1 < Q; ++l) {
+                if (took[side][l] < 0) continue;
+                const int64_t x2 = (int64_t)took[side][l] + pF[side][l];
+                if (x2 >= 0 && x2 < P && took[side][l + 1] == x2) fwd |= 1u << (2 * l + side);
+            }
+        pattern.push_back(fwd);
         for (int l = 0; l < Q; ++l) {
-            const uint32_t bits = word >> (2 * l) & 3u;
-            if (bits & 1u) { known[(size_t)l * P + a[l]] = 1; ++a[l]; --remaining; }
-            if (bits & 2u) { known[(size_t)l * P + z[l]] = 1; --z[l]; --remaining; }
+            if (took[0][l] >= 0) { known[(size_t)l * P + a[l]] = 1; ++a[l]; --remaining; }
+            if (took[1][l] >= 0) { known[(size_t)l * P + z[l]] = 1; --z[l]; --remaining; }
         }
         steps.push_back(word);
     }
-    if (out) {
-        out->T = (int)steps.size();
-        out->steps = std::move(steps);
-        for (int l = 0; l < Q; ++l) {
-            const int iL = asc[l], iR = asc[Q - 1 - l];
-            out->projL[l] = iL;
-            out->projR[l] = iR;
-            out->pL[l] = pl.p[iL];
-            out->pR[l] = pl.p[iR];
-            out->split[l] = a[l];
-            // bin j = l p - x - b_min at word off + j of the stripe block
-            out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
-            out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
-        }
+    // Steady steps: every front of every line moves and the operand pattern
+    // is the schedule's most common one among such steps. The device runs
+    // those with no per-line tests, forwarding exactly where `fwd` says.
+    const uint32_t all = Q >= 16 ? 0xFFFFFFFFu : (1u << (2 * Q)) - 1u;
+    uint32_t fwd = 0;
+    if (Q <= kFastMaxLines) {
+        std::map<uint32_t, int> count;
+        int best = 0;
+        for (size_t t = 0; t < steps.size(); ++t)
+            if (steps[t] == all && ++count[pattern[t]] > best) {
+                best = count[pattern[t]];
+                fwd = pattern[t];
+            }
+        if (best > 0)
+            for (size_t t = 0; t < steps.size(); ++t)
+                if (steps[t] == all && pattern[t] == fwd) steps[t] |= kStepSteady;
     }
-    return out ? out->T : (int)steps.size();
+    out->fwd = fwd;
+    out->T = (int)steps.size();
+    out->steps = std::move(steps);
+    out->fwdw = std::move(pattern);
+    for (int l = 0; l < Q; ++l) {
+        const int iL = asc[l], iR = asc[Q - 1 - l];
+        out->projL[l] = iL;
+        out->projR[l] = iR;
+        out->pL[l] = pl.p[iL];
+        out->pR[l] = pl.p[iR];
+        out->split[l] = a[l];
+        // bin j = l p - x - b_min at word off + j of the stripe block
+        out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
+        out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
+    }
+    return out->T;
 }
 
 // Cap on the number of Q-subsets of the survivors tried per mask.
@@ -177,16 +220,20 @@ int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev)
         *dev = it->second;
         return 0;
     }
+    // device copy: the step words, then the forward words
     uint32_t *d = nullptr;
-    const size_t bytes = std::max<size_t>(4, sc.steps.size() * sizeof(uint32_t));
+    const size_t n = sc.steps.size();
+    const size_t bytes = std::max<size_t>(4, 2 * n * sizeof(uint32_t));
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e == cudaErrorMemoryAllocation) {
         record_cuda(e);
         return -ENOMEM;
     }
     if ((r = record_cuda(e))) return r;
-    if ((r = record_cuda(cudaMemcpy(d, sc.steps.data(), sc.steps.size() * sizeof(uint32_t),
-                                    cudaMemcpyHostToDevice)))) {
+    std::vector<uint32_t> both(2 * n);
+    std::copy(sc.steps.begin(), sc.steps.end(), both.begin());
+    std::copy(sc.fwdw.begin(), sc.fwdw.end(), both.begin() + n);
+    if ((r = record_cuda(cudaMemcpy(d, both.data(), 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice)))) {
         cudaFree(d);
         return r;
     }

@@ -83,6 +83,31 @@ __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
                  : "memory");
 }
 
+// Order this thread's earlier generic-proxy shared-memory writes before
+// later async-proxy (TMA) reads of them.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 1-D bulk copy shared -> global (TMA store), tracked in this thread's bulk
+// group. Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_store_1d(void *dst, uint32_t src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until every bulk store this thread issued has finished reading shared
+// memory (the writes to global memory may still be in flight).
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;" ::: "memory");
