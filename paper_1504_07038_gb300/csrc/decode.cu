@@ -301,6 +301,7 @@ struct LineParams {
     int T4;               // steps, rounded up to a multiple of 4
     const uint32_t *steps;   // T step words, then T forward words
     int T;
+    uint32_t fwd;            // forward pattern of the steady steps
     int32_t p[2 * kMaxLines];
     int32_t src[2 * kMaxLines];
     int32_t split[kMaxLines];
@@ -349,6 +350,27 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ LineP
         dk[k - 1] = (l2 - l) * colstep;
     }
 
+    // Steady steps: this lane's link (line l forwards from line l+1) and the
+    // link state after each scan round, from the schedule's steady pattern:
+    // after the round with stride d, line l is still linked iff it was, and
+    // line l+d was too.
+    const uint32_t sfw = ok ? (a.fwd >> ls) & 1u : 0u;
+    uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    {
+        uint32_t c[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (a.fwd >> (2 * j + side)) & 1u : 0u;
+#pragma unroll
+        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+            slink[r] = ok ? c[l] : 0u;
+            uint32_t nc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : (c[j] ? 0u : 0u);
+#pragma unroll
+            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+        }
+    }
+
     // Copy lanes: lane = xk * G + gg covers XK columns of G stripes.
     const int XK = 32 / G;
     const int xk = lane / G, gg = lane - xk * G;
@@ -374,7 +396,24 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ LineP
 
         uint32_t pos = start;
         for (int t = 0; t < a.T4; ++t) {
-            const uint32_t w = stepw[t], f = fwdw[t];
+            const uint32_t w = stepw[t];
+            if (w & kStepSteady) {
+                // steady: every line moves, links are the schedule's pattern
+                uint64_t v = ld_s64(pos);
+#pragma unroll
+                for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
+                if (Q > 1) v ^= ld_s64_if(pos + d0, (sfw & has_next) ^ 1u);
+#pragma unroll
+                for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                    if (slink[r]) v ^= tv;
+                }
+                st_s64_if(pos, v, ok);
+                pos += stepb;
+                __syncwarp();
+                continue;
+            }
+            const uint32_t f = fwdw[t];
             const uint32_t act = w & bitmask;
             const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
             uint64_t v = ld_s64(pos);
@@ -481,6 +520,7 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         b.SWc = a.SWc;
         b.G = std::max(1, 32 / (2 * d.Q));
         b.T = d.T;
+        b.fwd = d.fwd;
         b.T4 = a.T4;
         b.steps = d.steps;
         for (int i = 0; i < 2 * d.Q; ++i) {

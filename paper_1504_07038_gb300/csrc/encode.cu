@@ -16,6 +16,7 @@
 // stores are consecutive 8-byte words across the warp.
 #include <algorithm>
 #include <cerrno>
+#include <cstdlib>
 
 #include "ptx.cuh"
 
@@ -24,7 +25,10 @@ namespace {
 
 constexpr int kEncThreads = 256;
 constexpr int kEncStages = 3;
-constexpr int kEncTileBytes = 16384;
+// Target bytes of a tile (measured on GB300: one stripe per tile is best at
+// Q <= 4, about two at Q = 8).
+constexpr int kEncTileBytesNarrow = 9000;
+constexpr int kEncTileBytesWide = 24000;
 
 struct EncParams {
     const uint64_t *img;
@@ -33,82 +37,96 @@ struct EncParams {
     int64_t ntiles;
     int total;
     int P, Q, n;
+    int pad;      // zero words before, between and after the rows of a stripe
+    int RP;       // row pitch in shared memory: P + pad (even when bulk)
+    int SWs;      // shared words per stripe: Q * RP + pad
     int spt;      // stripes per tile
     int stages;   // tiles in flight per CTA (bulk path)
-    int bulk;     // 1: TMA bulk copies; 0: 8-byte cp.async (odd Q*P)
+    int bulk;     // 1: one TMA bulk copy per row (P even); 0: 8-byte cp.async
     int32_t p[kMaxProj];
     int32_t off[kMaxProj];
     int32_t bmin[kMaxProj];
     uint32_t *status;
 };
 
-// XOR of the pixels on one discrete line: x = c + l p on line l.
+// Bin (c, p) of a stripe staged at byte address `a0` (its row 0, column c)
+// collects the word at a0 + l * stepc on every line l; pixels outside the
+// image read the zero pad columns.
 template <int QT>
-__device__ __forceinline__ uint64_t line_xor(const uint64_t *img, int Q, int P, int c, int p)
+__device__ __forceinline__ uint64_t line_xor(const char *sbase, uint32_t a0, int stepc, int Q)
 {
     uint64_t acc = 0;
     if (QT) {
 #pragma unroll
-        for (int l = 0; l < QT; ++l) {
-            const int x = c + l * p;
-            if ((unsigned)x < (unsigned)P) acc ^= img[l * P + x];
-        }
+        for (int l = 0; l < QT; ++l) acc ^= *reinterpret_cast<const uint64_t *>(sbase + a0 + l * stepc);
     } else {
-        for (int l = 0; l < Q; ++l) {
-            const int x = c + l * p;
-            if ((unsigned)x < (unsigned)P) acc ^= img[l * P + x];
-        }
+        for (int l = 0; l < Q; ++l) acc ^= *reinterpret_cast<const uint64_t *>(sbase + a0 + l * stepc);
     }
     return acc;
 }
 
 template <int QT, int ITEMS>
-__global__ void __launch_bounds__(kEncThreads)
+__global__ void __launch_bounds__(kEncThreads, 2)
 encode_tiles(const __grid_constant__ EncParams a)
 {
     extern __shared__ __align__(128) uint64_t sm[];
     const int Q = QT ? QT : a.Q;
-    const int P = a.P;
-    const int QP = Q * P;
-    const int tileWords = a.spt * QP;
+    const int P = a.P, RP = a.RP, SWs = a.SWs;
+    const int tileWords = a.spt * SWs;
     uint64_t *bars = sm + (size_t)a.stages * tileWords;
     const int tid = threadIdx.x;
+    const char *sbase = reinterpret_cast<const char *>(sm);
+
+    // zero every pad column of every stage once; rows are always staged
+    // before they are read, pads never written
+    for (int st = 0; st < a.stages; ++st)
+        for (int s = 0; s < a.spt; ++s) {
+            uint64_t *w = sm + (size_t)st * tileWords + (size_t)s * SWs;
+            for (int l = 0; l <= Q; ++l)
+                for (int i = tid; i < a.pad; i += kEncThreads) w[l * RP + i] = 0;
+        }
 
     // Output words t = tid + k * kEncThreads of every stripe: projection i
-    // (the last with off_i <= t) and c = -(j + b_min_i).
-    int c[ITEMS], pp[ITEMS];
+    // (the last with off_i <= t); the bin's pixel on line l sits at column
+    // c + l p_i with c = -(j + b_min_i), i.e. at byte a0 + l * stepc.
+    uint32_t a0[ITEMS];
+    int stepc[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
         const int t = tid + k * kEncThreads;
         int i = 0;
         for (int q = 1; q < a.n; ++q)
             if (a.off[q] <= t) i = q;
-        c[k] = -(t - a.off[i]) - a.bmin[i];
-        pp[k] = a.p[i];
+        const int c = -(t - a.off[i]) - a.bmin[i];
+        a0[k] = (uint32_t)((a.pad + c) * 8);
+        stepc[k] = (RP + a.p[i]) * 8;
     }
+    __syncthreads();
 
-    auto compute = [&](const uint64_t *buf, int64_t s0, int nst) {
+    auto compute = [&](int stage, int64_t s0, int nst) {
         for (int s = 0; s < nst; ++s) {
-            const uint64_t *img = buf + s * QP;
+            const uint32_t sb = (uint32_t)(((size_t)stage * tileWords + (size_t)s * SWs) * 8);
             uint64_t *out = a.proj + (s0 + s) * (int64_t)a.total;
 #pragma unroll
             for (int k = 0; k < ITEMS; ++k) {
                 const int t = tid + k * kEncThreads;
-                if (t < a.total) __stcs(out + t, line_xor<QT>(img, Q, P, c[k], pp[k]));
+                if (t < a.total) __stcs(out + t, line_xor<QT>(sbase, sb + a0[k], stepc[k], Q));
             }
         }
     };
 
     if (!a.bulk) {
-        // Unaligned tiles (odd Q*P): 8-byte asynchronous copies, one tile at a time.
+        // odd P: 8-byte asynchronous copies into the padded rows, one tile at a time
         for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
             const int64_t s0 = tile * a.spt;
             const int nst = (int)min64(a.spt, a.S - s0);
-            const uint64_t *src = a.img + s0 * QP;
-            for (int w = tid; w < nst * QP; w += kEncThreads) cp_async8(sm + w, src + w);
+            for (int w = tid; w < nst * Q * P; w += kEncThreads) {
+                const int s = w / (Q * P), r = w - s * Q * P, l = r / P, x = r - l * P;
+                cp_async8(sm + (size_t)s * SWs + a.pad + l * RP + x, a.img + (s0 + s) * (int64_t)Q * P + r);
+            }
             cp_async_wait_all();
             __syncthreads();
-            compute(sm, s0, nst);
+            compute(0, s0, nst);
             __syncthreads();
         }
         return;
@@ -120,13 +138,17 @@ encode_tiles(const __grid_constant__ EncParams a)
     }
     __syncthreads();
 
+    // One bulk copy per row of every stripe of the tile, all completing on
+    // the stage's mbarrier.
     auto issue = [&](int64_t tile, int stage) {
         const int64_t s0 = tile * a.spt;
         const int nst = (int)min64(a.spt, a.S - s0);
-        const uint32_t bytes = (uint32_t)nst * (uint32_t)QP * 8u;
         const uint32_t bar = smem_addr(bars + stage);
-        mbar_arrive_expect_tx(bar, bytes);
-        tma_load_1d(smem_addr(sm + (size_t)stage * tileWords), a.img + s0 * QP, bytes, bar);
+        mbar_arrive_expect_tx(bar, (uint32_t)nst * (uint32_t)Q * (uint32_t)P * 8u);
+        for (int s = 0; s < nst; ++s)
+            for (int l = 0; l < Q; ++l)
+                tma_load_1d(smem_addr(sm + (size_t)stage * tileWords + (size_t)s * SWs + a.pad + l * RP),
+                            a.img + ((s0 + s) * (int64_t)Q + l) * P, (uint32_t)P * 8u, bar);
     };
 
     int64_t issued = 0;   // tiles issued by thread 0 (counted in this CTA's order)
@@ -156,7 +178,7 @@ encode_tiles(const __grid_constant__ EncParams a)
             }
         }
         const int64_t s0 = tile * a.spt;
-        compute(sm + (size_t)stage * tileWords, s0, (int)min64(a.spt, a.S - s0));
+        compute(stage, s0, (int)min64(a.spt, a.S - s0));
     }
     if (timed_out && tid == 0) {
         atomicOr(a.status, kStatusWaitTimeout);
@@ -257,12 +279,22 @@ int launch_encode(const EncodeArgs &e, cudaStream_t st)
     const int smem_cap = max_dyn_smem(&err);
     if (err) return err;
 
-    const int64_t QP = (int64_t)e.Q * e.P;
-    const int64_t stripe_bytes = QP * 8;
+    int maxp = 0;
+    for (int i = 0; i < e.n; ++i) maxp = std::max(maxp, e.p[i] < 0 ? -e.p[i] : e.p[i]);
     const int64_t need = (e.total + kEncThreads - 1) / kEncThreads;
     const int items = need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 16 ? 16 : 0;
-    a.bulk = (QP % 2 == 0) ? 1 : 0;
-    a.spt = (int)std::max<int64_t>(1, kEncTileBytes / stripe_bytes);
+    a.bulk = (e.P % 2 == 0) ? 1 : 0;
+    // Zero columns around the rows cover every offset l p of a bin line, so
+    // no bounds test sits in the inner loop; with bulk copies the pad and row
+    // pitch are even so that every row starts 16-byte aligned.
+    a.pad = (e.Q - 1) * maxp;
+    if (a.bulk && a.pad % 2) ++a.pad;
+    a.RP = e.P + a.pad;
+    a.SWs = e.Q * a.RP + a.pad;
+    const int64_t stripe_bytes = (int64_t)a.SWs * 8;
+    int64_t tile_bytes = e.Q <= 4 ? kEncTileBytesNarrow : kEncTileBytesWide;
+    if (const char *env = getenv("MOJETTE_ENCODE_TILE")) tile_bytes = std::max(1, atoi(env));   // tuning
+    a.spt = (int)std::max<int64_t>(1, tile_bytes / stripe_bytes);
     a.stages = a.bulk ? kEncStages : 1;
     auto smem_of = [&](void) {
         return (int64_t)a.stages * a.spt * stripe_bytes + (a.bulk ? 8 * a.stages : 0);
