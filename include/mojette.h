@@ -26,7 +26,8 @@
  *       -ENOMEM           host or device allocation failed;
  *       -EIO              a CUDA runtime error (see mojette_last_cuda_error);
  *       -ETIMEDOUT        a bounded device-side wait expired (reported by
- *                         mojette_device_status).
+ *                         mojette_device_status);
+ *       -ENOSPC           a schedule too large for mojette_decode_noalloc.
  *   - Device buffers (d_*) are owned by the caller, live in the current
  *     device's memory, and must not overlap each other. Work is enqueued on
  *     `stream` (a cudaStream_t; NULL = legacy default stream) and is
@@ -109,6 +110,30 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
 int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
                    uint32_t erasure_mask, uint64_t *d_img, int64_t S,
                    mojette_stream_t stream);
+
+/*
+ * mojette_decode_noalloc -- mojette_decode for callers that must not allocate
+ * device memory. The paper has no counterpart: this is a library concern.
+ * Some callers cannot call cudaMalloc: a storage server that hands all of its
+ * device memory to its own buffer pool at start-up, or a request path that
+ * must not take the device-wide synchronisation cudaMalloc may cause. This
+ * call allocates nothing on the device (no cudaMalloc, cudaFree or
+ * allocating library routine). The reconstruction path's step words go to a
+ * fixed scratch array inside the library, 2 * 16384 words (128 KiB), that
+ * every GPU loading the library holds until the process exits; schedules of
+ * more than 16384 steps are refused with -ENOSPC. The caller still passes the
+ * inputs and outputs, as for mojette_decode.
+ * Every call shares that scratch and overwrites it (on `stream`, before the
+ * kernel): calls that can overlap on the GPU -- on different streams without
+ * ordering between them -- race and may decode with another call's path.
+ * Order such calls on one stream, or use mojette_decode. The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress), a
+ * set-up step; make that first call outside any stream capture.
+ * Errors: as mojette_decode, plus -ENOSPC.
+ */
+int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
+                           uint32_t erasure_mask, uint64_t *d_img, int64_t S,
+                           mojette_stream_t stream);
 
 /*
  * mojette_schedule -- the cached reconstruction path for one erasure mask,

@@ -49,13 +49,15 @@ def lib():
             L.mojette_plan_info.argtypes = [_PTR, _PTR, _PTR, _PTR]
             L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
+            L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_device_status.argtypes = [ctypes.POINTER(_U32), _INT]
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
             L.mojette_last_cuda_error.argtypes = []
             for name in ("mojette_plan", "mojette_plan_destroy", "mojette_plan_info",
-                         "mojette_encode", "mojette_decode", "mojette_schedule",
+                         "mojette_encode", "mojette_decode", "mojette_decode_noalloc",
+                         "mojette_schedule",
                          "mojette_device_status", "mojette_last_cuda_error"):
                 getattr(L, name).restype = _INT
             _lib = L
@@ -165,6 +167,17 @@ def mojette_decode(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None =
         S = d_img.numel() // (plan.P * plan.Q)
     _check(lib().mojette_decode(plan.handle, _addr(d_proj), int(erasure_mask) & 0xFFFFFFFF,
                                 _addr(d_img), int(S), _stream(stream)), "mojette_decode")
+
+
+def mojette_decode_noalloc(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None = None,
+                           stream=None) -> None:
+    """mojette_decode without any device allocation (fixed in-library scratch;
+    calls that overlap on the GPU race -- see include/mojette.h)."""
+    if S is None:
+        S = d_img.numel() // (plan.P * plan.Q)
+    _check(lib().mojette_decode_noalloc(plan.handle, _addr(d_proj), int(erasure_mask) & 0xFFFFFFFF,
+                                        _addr(d_img), int(S), _stream(stream)),
+           "mojette_decode_noalloc")
 
 
 def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:

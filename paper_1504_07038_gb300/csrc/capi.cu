@@ -171,6 +171,44 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     return launch_decode(a, (cudaStream_t)stream);
 }
 
+int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure_mask,
+                           uint64_t *d_img, int64_t S, mojette_stream_t stream)
+{
+    if (!plan || S < 0) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->Q > kMaxLines) return -EINVAL;
+    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);   // host memory only
+    if (!sc) return err;
+    if (sc->T > kNoAllocMaxSteps) return -ENOSPC;
+    if (S == 0) return 0;
+    if (!d_img || !d_proj) return -EINVAL;
+    if (!aligned16(d_img) || !aligned16(d_proj)) return -ERANGE;
+    uint32_t *dsteps = nullptr;
+    if ((err = noalloc_schedule_copy(*sc, (cudaStream_t)stream, &dsteps))) return err;
+    DecodeArgs a;
+    a.proj = d_proj;
+    a.img = d_img;
+    a.S = S;
+    a.total = pl->total;
+    a.P = pl->P;
+    a.Q = pl->Q;
+    a.T = sc->T;
+    a.steps = dsteps;
+    a.fwd = sc->fwd;
+    for (int l = 0; l < pl->Q; ++l) {
+        a.pL[l] = sc->pL[l];
+        a.pR[l] = sc->pR[l];
+        a.split[l] = sc->split[l];
+        a.srcL[l] = sc->srcL[l];
+        a.srcR[l] = sc->srcR[l];
+    }
+    a.status = device_status_ptr(&err);
+    if (err) return err;
+    return launch_decode(a, (cudaStream_t)stream);
+}
+
 int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *survivors,
                      int32_t *survivors2, int32_t *split, uint32_t *steps,
                      uint32_t *forward, int64_t max_steps, int64_t *n_steps)
@@ -218,6 +256,7 @@ const char *mojette_strerror(int status)
     case -ENOMEM: return "out of memory";
     case -EIO: return "CUDA runtime error (see mojette_last_cuda_error)";
     case -ETIMEDOUT: return "a bounded device-side wait expired";
+    case -ENOSPC: return "schedule larger than the fixed scratch of mojette_decode_noalloc";
     default: return "unknown status";
     }
 }

@@ -30,6 +30,8 @@
 #include <cerrno>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "ptx.cuh"
 
@@ -576,4 +578,48 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     return record_cuda(cudaGetLastError());
 }
 
+
+// ---------------------------------------------------------------------------
+// Scratch for mojette_decode_noalloc: the step words and forward words of one
+// schedule, in a fixed array that every GPU loading the library holds until
+// the process exits (2 * kNoAllocMaxSteps * 4 bytes = 128 KiB). In host code
+// the name of the array is only a stand-in; the device address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) uint32_t g_noalloc_steps[2 * kNoAllocMaxSteps];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::map<int, uint32_t *> g_noalloc_ptr;
+}  // namespace
+
+int noalloc_schedule_copy(const Schedule &sc, cudaStream_t st, uint32_t **dev)
+{
+    if (sc.T > kNoAllocMaxSteps) return -ENOSPC;
+    int device = 0, err = 0;
+    if ((err = record_cuda(cudaGetDevice(&device)))) return err;
+    uint32_t *ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        auto it = g_noalloc_ptr.find(device);
+        if (it != g_noalloc_ptr.end()) {
+            ptr = it->second;
+        } else {
+            if ((err = record_cuda(cudaGetSymbolAddress((void **)&ptr, g_noalloc_steps)))) return err;
+            g_noalloc_ptr[device] = ptr;
+        }
+    }
+    // Step words then forward words, packed at stride T as the kernels read
+    // them. Pageable host memory: the runtime has taken its own copy of both
+    // vectors when cudaMemcpyAsync returns.
+    const size_t bytes = sc.steps.size() * sizeof(uint32_t);
+    if (bytes) {
+        if ((err = record_cuda(cudaMemcpyAsync(ptr, sc.steps.data(), bytes, cudaMemcpyHostToDevice, st))))
+            return err;
+        if ((err = record_cuda(cudaMemcpyAsync(ptr + sc.steps.size(), sc.fwdw.data(), bytes,
+                                               cudaMemcpyHostToDevice, st))))
+            return err;
+    }
+    *dev = ptr;
+    return 0;
+}
 }  // namespace mojette

@@ -97,4 +97,10 @@ struct DecodeArgs {
 };
 int launch_decode(const DecodeArgs &a, cudaStream_t stream);
 
+// Largest schedule (in steps) mojette_decode_noalloc accepts.
+constexpr int kNoAllocMaxSteps = 16384;
+// Copy a schedule's words into the fixed device scratch of decode.cu (on
+// `stream`) and return its device address; no device allocation.
+int noalloc_schedule_copy(const Schedule &sc, cudaStream_t stream, uint32_t **dev);
+
 }  // namespace mojette
