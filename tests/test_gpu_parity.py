@@ -207,3 +207,30 @@ def test_full_size_wide_geometry():
     ms = inputs.all_masks(12, 4)
     _full_size(64, 8, TWELVE, 262144, ms[::61])
     _full_size(128, 8, TWELVE, 262144, ms[7::83])
+
+
+VARIANTS = [("lines", None), ("fronts", None)]
+
+
+@pytest.mark.parametrize("kernel,K", VARIANTS)
+@pytest.mark.parametrize("name,P,Q,p", [GEOMS[0], GEOMS[2], GEOMS[3], GEOMS[4]]
+                         + [("tiny(6,3)", 20, 3, [-4, -1, 0, 2, 5, 6]),
+                            ("odd P(8,6)", 33, 6, [-4, -3, -1, 1, 2, 3, 5, 7])])
+def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
+    """Each decode kernel (decode_lines, decode_fronts), every k-of-n mask
+    (sampled at (12,8)), bit-exact."""
+    monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+    S = 53
+    n = len(p)
+    img = inputs.stripes(S, Q, P, seed=P + Q)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    d_proj = dev(proj)
+    out = empty((S, Q, P))
+    masks = inputs.all_masks(n, n - Q)
+    masks = masks if len(masks) <= 60 else masks[::9]
+    masks += inputs.all_masks(n, 0)
+    for m in masks:
+        out.fill_(0x77)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        assert (host(out) == img).all(), (kernel, K, name, m)
