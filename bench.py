@@ -54,6 +54,13 @@ WORKLOADS = {
     "wide_8k": dict(P=128, Q=8, p=TWELVE, S=262144, erasures=4, mask_sample=15,
                     desc="262144 stripes x 8 KB (Q=8, P=128), (12,8); encode + 15 four-erasure decodes"),
 }
+# Mixed batch: 4 KB and 8 KB stripes of the (3,2), (6,4) and (12,8) codes.
+BATCH_GEOMS = [(256, 2, [-1, 1, 2]), (512, 2, [-1, 1, 2]), (128, 4, SIX), (256, 4, SIX),
+               (64, 8, TWELVE), (128, 8, TWELVE)]
+BATCHED = dict(S=500000,
+                            desc="500000 stripes, seeded mix of 4 KB / 8 KB x (3,2) p={-1,1,2}, (6,4) "
+                                 "p=+-1..3, (12,8) p=+-1..6, 0..n-k seeded erasures each, random order; "
+                                 "one step = encode every stripe, then decode every stripe")
 METRIC = "Mojette encode/decode user-data GB/s & % HBM roofline; batched vs plain, 1 GB300"
 KERNEL_SOURCES = ["encode.cu", "decode.cu", "ptx.cuh", "mojette_internal.h"]
 
@@ -167,6 +174,24 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_first_stripe(rank: int, S: int) -> int:
+    """Replicas: rank r encodes and decodes stripes r*S .. r*S + S - 1 of the
+    seeded stream (weak scaling: the same work per GPU, disjoint data, no
+    exchange between ranks)."""
+    return rank * S
+
+
+def max_over_ranks(x: float, dist=None) -> float:
+    """The slowest rank's time (every rank gets it); x itself on one GPU."""
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------ GPU arm --
 
 def run_gpu(args, w):
@@ -185,7 +210,7 @@ def run_gpu(args, w):
     plan = mj.mojette_plan(P, Q, p)
     stream = torch.cuda.current_stream()
 
-    img_np = inputs.stripes(S, Q, P, first=rank * S)     # each rank its own stripes
+    img_np = inputs.stripes(S, Q, P, first=replica_first_stripe(rank, S))
     h_img = torch.from_numpy(img_np.view(np.int64)).pin_memory()
     del img_np
     d_img = h_img.cuda()
@@ -241,10 +266,7 @@ def run_gpu(args, w):
     dec_ms = [a.elapsed_time(b) for e in events for a, b in e[1:]]
     total_ms = t0.elapsed_time(t1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     mj.mojette_device_status()
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -305,6 +327,10 @@ def run_gpu(args, w):
         "clocks": clk,
         "e2e": e2e,
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, rank)
+    if not args.no_served:
+        line["served"] = run_served(args, rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, masks, budget_s=args.cpu_seconds)
     if dist:
@@ -350,6 +376,149 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
             "h2d_bytes_per_step": S * Q * P * 8 + len(masks) * S * plan.total * 8,
             "d2h_bytes_per_step": S * plan.total * 8 + len(masks) * S * Q * P * 8,
             "ms_per_step": round(ms, 3), "steps": steps, "round_trip_ok": ok}
+
+
+# ------------------------------------------------------------ batched arm --
+
+def run_batched(args, rank=0):
+    """The mixed batch two ways on the same device buffers: (a) batched --
+    one CUDA-graph launch for every encode and one for every decode (after
+    autotuning); (b) plain -- one mojette_encode per geometry and one
+    mojette_decode per (geometry, erasure mask), stripes of a mask
+    contiguous. Returns a dict of both throughputs (user data, encode +
+    decode per step) and the round-trip checks."""
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
+
+    S = BATCHED["S"]
+    seed = inputs.DEFAULT_SEED + 1000 * rank
+    cat = inputs.categories(S, len(BATCH_GEOMS), seed=seed)
+    plans, d_img, d_proj, d_out, groups = [], [], [], [], []
+    enc_parts, dec_parts = [], []
+    user = 0
+    for k, (P, Q, p) in enumerate(BATCH_GEOMS):
+        Sk = int((cat == k).sum())
+        plan = mj.mojette_plan(P, Q, p)
+        n = len(p)
+        masks = inputs.erasure_masks(Sk, n, inputs.erasure_counts(Sk, n - Q, seed=seed + k), seed=seed + k)
+        masks = np.sort(masks, kind="stable")          # stripes of a mask contiguous (plain arm)
+        img = torch.from_numpy(inputs.stripes(Sk, Q, P, seed=seed + 17 * k).view(np.int64)).cuda()
+        proj = torch.empty((Sk, plan.total), dtype=torch.int64, device="cuda")
+        out = torch.empty((Sk, Q, P), dtype=torch.int64, device="cuda")
+        plans.append(plan)
+        d_img.append(img)
+        d_proj.append(proj)
+        d_out.append(out)
+        uniq, start = np.unique(masks, return_index=True)
+        ends = list(start[1:]) + [Sk]
+        groups.append([(int(m), int(a), int(b)) for m, a, b in zip(uniq, start, ends)])
+        s_idx = np.arange(Sk, dtype=np.uint64)
+        enc_parts.append((np.full(Sk, k), np.zeros(Sk, np.uint32), img.data_ptr() + s_idx * np.uint64(Q * P * 8),
+                          proj.data_ptr() + s_idx * np.uint64(plan.total * 8)))
+        dec_parts.append((np.full(Sk, k), masks, proj.data_ptr() + s_idx * np.uint64(plan.total * 8),
+                          out.data_ptr() + s_idx * np.uint64(Q * P * 8)))
+        user += Sk * Q * P * 8
+
+    def table(parts, op):
+        perm = inputs.permutation(S, seed=seed + op)
+        cols = [np.concatenate([pt[c] for pt in parts])[perm] for c in range(4)]
+        return mj.stripe_table(plans, cols[0], op, cols[1], cols[2], cols[3])
+
+    stream = torch.cuda.current_stream()
+    enc = mj.mojette_batch_create(table(enc_parts, mj.MOJETTE_OP_ENCODE), plans, mj.MOJETTE_BATCH_GRAPH)
+    dec = mj.mojette_batch_create(table(dec_parts, mj.MOJETTE_OP_DECODE), plans, mj.MOJETTE_BATCH_GRAPH)
+    mj.mojette_batch_run(enc, stream)
+    t0 = time.perf_counter()
+    mj.mojette_batch_tune(enc, stream, reps=2)
+    mj.mojette_batch_tune(dec, stream, reps=2)
+    tune_s = time.perf_counter() - t0
+
+    def step_batched():
+        mj.mojette_batch_run(enc, stream)
+        mj.mojette_batch_run(dec, stream)
+
+    def step_plain():
+        for k, plan in enumerate(plans):
+            mj.mojette_encode(plan, d_img[k], d_proj[k], d_img[k].shape[0], stream)
+        for k, plan in enumerate(plans):
+            for m, a, b in groups[k]:
+                mj.mojette_decode(plan, d_proj[k][a:b], m, d_out[k][a:b], b - a, stream)
+
+    def timed(step):
+        for t in d_out:
+            t.zero_()
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ok = all(torch.equal(o, i) for o, i in zip(d_out, d_img))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(3, min(args.steps, 10))
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, ok, steps
+
+    ms_b, ok_b, steps_b = timed(step_batched)
+    ms_p, ok_p, steps_p = timed(step_plain)
+    mj.mojette_device_status()
+    ie, idd = mj.mojette_batch_info(enc), mj.mojette_batch_info(dec)
+    plain_launches = len(plans) + sum(len(g) for g in groups)
+    return {"value": round(2 * user / (ms_b * 1e-3) / 1e9, 3), "unit": "GB/s",
+            "ms_per_step": round(ms_b, 4), "steps": steps_b, "round_trip_ok": ok_b,
+            "plain": {"value": round(2 * user / (ms_p * 1e-3) / 1e9, 3), "ms_per_step": round(ms_p, 4),
+                      "launches_per_step": plain_launches, "round_trip_ok": ok_p, "steps": steps_p},
+            "speedup_vs_plain": round(ms_p / ms_b, 3),
+            "workload": BATCHED["desc"], "stripes": S, "user_bytes_per_op": user,
+            "graph_launches_per_step": 2, "kernels_per_step": ie["launches"] + idd["launches"],
+            "decode_groups": idd["groups"], "tune_s": round(tune_s, 2),
+            "tuned": {"encode": ie["configs"], "decode": idd["configs"]},
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------- served arm --
+
+SERVED = dict(requests=3000, budget=16 << 30, slots=4, max_wave_stripes=65536,
+              desc="request server: 70% writes / 30% reads (0..n-k seeded erasures), objects 4 KB-1 MB "
+                   "log-uniform in 4 KB / 8 KB stripes of (6,4) or (12,8), pinned host buffers, "
+                   "16 GB device budget; closed loop for capacity, Poisson arrivals at 50/80/95% of it")
+
+
+def run_served(args, rank=0):
+    """The request server against the same requests served one at a time
+    through the plain entry points. Throughput = object bytes / elapsed
+    (first arrival to last completion), copies included."""
+    from paper_1504_07038_gb300 import binding as mj
+    from paper_1504_07038_gb300 import serving
+
+    cfg = SERVED
+    wl = serving.Workload(cfg["requests"], seed=inputs.DEFAULT_SEED + 7 + 1000 * rank)
+    srv = mj.mojette_server_create(cfg["budget"], cfg["slots"], cfg["max_wave_stripes"])
+    user = float(wl.user_bytes.sum())
+    serving.run_server(srv, wl, rate=None)                    # warm-up: batches, schedules
+    comp, el = serving.run_server(srv, wl, rate=None)
+    ok = all(np.array_equal(wl.output(r), (wl.images[r].reshape(-1))) for r in range(len(wl))
+             if not wl.write[r])
+    cap_rps = len(wl) / el
+    out = {"closed_loop": {"value": round(user / el / 1e9, 3), "unit": "GB/s", "requests_per_s": round(cap_rps, 1),
+                           **serving.latency_stats(comp)},
+           "reads_ok": ok, "requests": len(wl), "user_bytes": int(user),
+           "write_fraction": round(float(wl.write.mean()), 3), "workload": cfg["desc"]}
+    for frac in (0.5, 0.8, 0.95):
+        comp, el = serving.run_server(srv, wl, rate=frac * cap_rps, seed=int(frac * 100))
+        out[f"poisson_{int(frac * 100)}pct"] = {"offered_rps": round(frac * cap_rps, 1),
+                                                "value": round(user / el / 1e9, 3), "unit": "GB/s",
+                                                **serving.latency_stats(comp)}
+    st = mj.mojette_server_stats(srv)
+    out["waves"] = st["waves"]
+    out["pool_peak_bytes"] = st["pool_peak"]
+    el_plain = serving.run_plain(wl)
+    out["plain_sequential"] = {"value": round(user / el_plain / 1e9, 3), "unit": "GB/s",
+                               "requests_per_s": round(len(wl) / el_plain, 1)}
+    out["speedup_vs_plain"] = round(out["closed_loop"]["value"] / out["plain_sequential"]["value"], 3)
+    srv.close()
+    return out
 
 
 # --------------------------------------------------------------- CPU oracle --
@@ -418,6 +587,8 @@ def main():
     ap.add_argument("--workload", default="plain_at_scale", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -161,6 +161,191 @@ int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask,
                      uint32_t *steps, uint32_t *forward, int64_t max_steps,
                      int64_t *n_steps);
 
+/* ------------------------------------------------------------------------
+ * Batches: many stripes of mixed geometry, operation (encode or decode) and
+ * erasure pattern in one submission. The paper codes one block at a time
+ * (Sec. 4); batching is a library concern with no counterpart there. Each
+ * stripe's result is bit-identical to what mojette_encode / mojette_decode
+ * give for it alone.
+ * ------------------------------------------------------------------------ */
+
+#define MOJETTE_OP_ENCODE 0
+#define MOJETTE_OP_DECODE 1
+
+/* One stripe of a batch. */
+typedef struct mojette_stripe {
+    mojette_plan_t plan;     /* its geometry; must outlive the batch */
+    int32_t op;              /* MOJETTE_OP_ENCODE or MOJETTE_OP_DECODE */
+    uint32_t erasure_mask;   /* decode: bit i set = projection i lost; else 0 */
+    const uint64_t *src;     /* device, 8-byte aligned (16-byte for an
+                                encode with P even): encode reads the
+                                [Q][P] pixels, decode the [total] bins */
+    uint64_t *dst;           /* device, 8-byte aligned: encode writes the
+                                [total] bins, decode the [Q][P] pixels */
+} mojette_stripe_t;
+
+/* Opaque batch: the stripes' device tables, side streams, an optional CUDA
+ * graph. Not thread-safe: one host thread at a time per batch. */
+typedef struct mojette_batch_s *mojette_batch_t;
+
+/* mojette_batch_create flag: mojette_batch_run launches one CUDA graph
+ * (captured on the first run after the stripes change) instead of one kernel
+ * launch per (operation, plan). */
+#define MOJETTE_BATCH_GRAPH 1u
+
+/*
+ * mojette_batch_create -- build a batch over count stripes (count >= 0).
+ * Stripes are grouped by (operation, plan) -- one kernel launch each -- and,
+ * for decode, by erasure mask -- one reconstruction path each (Sec. 2.2),
+ * computed and cached in the plan as by mojette_decode. Builds the device
+ * tables (per-stripe addresses, paths, work items: about 16 bytes per stripe
+ * plus 336 bytes per (plan, mask)) and uploads them; blocking. The stripes
+ * array is read, not retained. Buffers must not overlap between stripes
+ * whose writes could collide.
+ * Errors: -EINVAL (null plan or pointer, bad op, mask bits beyond n, decode
+ * with Q > MOJETTE_MAX_DECODE_LINES, unknown flag), -ERANGE (unaligned
+ * pointer), -ENOTRECOVERABLE (a mask leaves fewer than Q projections),
+ * -ENOMEM, -EIO.
+ */
+int mojette_batch_create(const mojette_stripe_t *stripes, int64_t count,
+                         uint32_t flags, mojette_batch_t *out);
+
+/*
+ * mojette_batch_update -- replace the stripes of a batch (same rules as
+ * mojette_batch_create). The tables are uploaded asynchronously on `stream`;
+ * later runs on any stream wait for that upload. Waits on the host for the
+ * previous update's upload to leave the pinned staging buffer. When the new
+ * tables do not fit the workspace it is reallocated, which synchronises the
+ * device. A batch must not be updated while one of its runs enqueued on
+ * another stream can still be executing.
+ */
+int mojette_batch_update(mojette_batch_t batch, const mojette_stripe_t *stripes,
+                         int64_t count, mojette_stream_t stream);
+
+/*
+ * mojette_batch_run -- enqueue every stripe of the batch on `stream`. The
+ * launches of the different (operation, plan) classes run concurrently on
+ * side streams (or graph branches) forked from and joined back into
+ * `stream`. Within a batch, stripes are independent: a decode reads its
+ * bins as they are when the run starts on the device.
+ * Errors: -EINVAL, -EIO.
+ */
+int mojette_batch_run(mojette_batch_t batch, mojette_stream_t stream);
+
+/*
+ * mojette_batch_tune -- autotune the launch configuration of every class of
+ * the batch: for decode the kernel (decode_lines, one lane per line and
+ * front; decode_stream, the same lanes with the stripe streamed through
+ * shared memory in chunks; decode_fronts, one lane per front), stripes per
+ * CTA, persistent or one-shot grids and the shared-memory row pitch; for
+ * encode the stripes per shared-memory tile. Each
+ * candidate runs 1 + reps times on `stream` (so the batch's outputs are
+ * written, with their correct values) and is timed with CUDA events; the
+ * fastest is kept in the batch and in the plan, where later batches of the
+ * plan start from it. Synchronises `stream`. Errors: -EINVAL, -EIO.
+ */
+int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps);
+
+/*
+ * mojette_batch_info -- the batch's shape (any pointer may be NULL):
+ *   launches    kernel launches per run (one per (operation, plan));
+ *   groups      (plan, mask) groups of the decode stripes;
+ *   work_items  decode work items (one warp's stripes each);
+ *   configs     6 words per launch: op, Q, P, then for decode the kernel
+ *               (0 decode_lines, 1 decode_fronts, 2 decode_stream), work
+ *               items per CTA and
+ *               flags (bit 0 persistent grid, bit 1 bank-spread row pitch),
+ *               for encode 0, the tile bytes (0 = default) and 0. The array
+ *               holds 6 * launches words.
+ */
+int mojette_batch_info(mojette_batch_t batch, int64_t *launches, int64_t *groups,
+                       int64_t *work_items, int32_t *configs);
+
+/* Release a batch (synchronises the device first). NULL is a no-op. */
+int mojette_batch_destroy(mojette_batch_t batch);
+
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of object writes (encode) and reads
+ * (decode) under a device-memory budget. Like batches, a library concern
+ * with no counterpart in the paper. Each request's result is bit-identical
+ * to mojette_encode / mojette_decode of its stripes alone.
+ * ------------------------------------------------------------------------ */
+
+/* One object write or read: `stripes` whole stripes of one plan. */
+typedef struct mojette_request {
+    uint64_t id;             /* caller's tag, returned in the completion */
+    mojette_plan_t plan;     /* must outlive the server */
+    int32_t op;              /* MOJETTE_OP_ENCODE (write) or _DECODE (read) */
+    uint32_t erasure_mask;   /* read: projections lost; write: ignored */
+    int64_t stripes;         /* >= 1 */
+    const void *host_src;    /* pinned host memory: write [stripes][Q][P]
+                                pixels, read [stripes][total] bins */
+    void *host_dst;          /* pinned host memory: write [stripes][total]
+                                bins, read [stripes][Q][P] pixels */
+    double arrival_s;        /* arrival time on the server clock
+                                (mojette_server_now); <= 0: at submission */
+} mojette_request_t;
+
+typedef struct mojette_completion {
+    uint64_t id;
+    int32_t status;          /* 0, or a negative errno for the request */
+    double arrival_s;        /* as submitted (or the submission time) */
+    double admit_s;          /* admitted into a wave: device memory reserved */
+    double done_s;           /* its wave's event seen complete (output in
+                                host_dst) */
+} mojette_completion_t;
+
+typedef struct mojette_server_s *mojette_server_t;
+
+/*
+ * mojette_server_create -- a server on the current device.
+ *   device_budget_bytes  the device buffer pool, allocated here once (the
+ *                        admission budget: a request holds its input and
+ *                        output stripes there while it is in flight);
+ *   slots                waves in flight at once (1..64), each with its own
+ *                        stream and batch;
+ *   max_wave_stripes     stripes per wave at most (bounds a wave's latency);
+ *                        a larger request is refused at submission.
+ * Errors: -EINVAL, -ENOMEM, -EIO.
+ */
+int mojette_server_create(int64_t device_budget_bytes, int slots,
+                          int64_t max_wave_stripes, mojette_server_t *out);
+
+/*
+ * mojette_server_submit -- queue n requests (first come, first served) and
+ * make progress. Never waits for the device. The request array is copied;
+ * the host buffers must stay valid (and host_dst unread) until the request
+ * completes. Admission: a wave takes queued requests in order while their
+ * buffers fit the pool; a request that does not fit waits (later requests
+ * wait behind it). Errors (nothing is queued): -EINVAL, -ENOTRECOVERABLE (a
+ * read's mask leaves fewer than Q projections), -ENOSPC (a request larger
+ * than the budget or than max_wave_stripes), or an error of a wave
+ * launched meanwhile (see mojette_server_poll).
+ */
+int mojette_server_submit(mojette_server_t server, const mojette_request_t *reqs,
+                          int64_t n);
+
+/*
+ * mojette_server_poll -- make progress (retire finished waves, admit and
+ * launch new ones into free slots) and return up to `max` completions in
+ * completion order. A wave that fails completes its requests with the
+ * error status, and the call returns that error too.
+ */
+int mojette_server_poll(mojette_server_t server, mojette_completion_t *out,
+                        int64_t max, int64_t *n_out);
+
+/* Seconds on the server's clock (steady, zero at creation). */
+int mojette_server_now(mojette_server_t server, double *seconds);
+
+/* Counters: requests queued and in flight, waves launched, requests
+ * completed, pool bytes in use and the peak. Any pointer may be NULL. */
+int mojette_server_stats(mojette_server_t server, int64_t *queued,
+                         int64_t *in_flight, int64_t *waves, int64_t *completed,
+                         int64_t *pool_used, int64_t *pool_peak);
+
+/* Wait for the waves in flight, then release the server. NULL is a no-op. */
+int mojette_server_destroy(mojette_server_t server);
+
 /*
  * mojette_device_status -- synchronise the current device and return the
  * sticky status word the kernels set (0 = clean; bit 0: a bounded wait for

@@ -17,6 +17,8 @@ import os
 import re
 import threading
 
+import numpy as np
+
 from . import build as _build
 
 _lock = threading.Lock()
@@ -51,13 +53,29 @@ def lib():
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
+            L.mojette_batch_create.argtypes = [_PTR, _I64, _U32, ctypes.POINTER(_PTR)]
+            L.mojette_batch_update.argtypes = [_PTR, _PTR, _I64, _PTR]
+            L.mojette_batch_run.argtypes = [_PTR, _PTR]
+            L.mojette_batch_tune.argtypes = [_PTR, _PTR, _INT]
+            L.mojette_batch_info.argtypes = [_PTR, _PTR, _PTR, _PTR, _PTR]
+            L.mojette_batch_destroy.argtypes = [_PTR]
+            L.mojette_server_create.argtypes = [_I64, _INT, _I64, ctypes.POINTER(_PTR)]
+            L.mojette_server_submit.argtypes = [_PTR, _PTR, _I64]
+            L.mojette_server_poll.argtypes = [_PTR, _PTR, _I64, ctypes.POINTER(_I64)]
+            L.mojette_server_now.argtypes = [_PTR, ctypes.POINTER(ctypes.c_double)]
+            L.mojette_server_stats.argtypes = [_PTR] + [ctypes.POINTER(_I64)] * 6
+            L.mojette_server_destroy.argtypes = [_PTR]
             L.mojette_device_status.argtypes = [ctypes.POINTER(_U32), _INT]
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
             L.mojette_last_cuda_error.argtypes = []
             for name in ("mojette_plan", "mojette_plan_destroy", "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc",
-                         "mojette_schedule",
+                         "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
+                         "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
+                         "mojette_batch_destroy", "mojette_server_create", "mojette_server_submit",
+                         "mojette_server_poll", "mojette_server_now", "mojette_server_stats",
+                         "mojette_server_destroy",
                          "mojette_device_status", "mojette_last_cuda_error"):
                 getattr(L, name).restype = _INT
             _lib = L
@@ -196,6 +214,169 @@ def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:
                                   steps, forward, T, ctypes.byref(nsteps)), "mojette_schedule")
     return {"left": list(left), "right": list(right), "split": list(split),
             "steps": list(steps)[:T], "forward": list(forward)[:T], "T": T}
+
+
+# ---- batches -----------------------------------------------------------------
+
+MOJETTE_OP_ENCODE = 0
+MOJETTE_OP_DECODE = 1
+MOJETTE_BATCH_GRAPH = 1
+
+# Layout of mojette_stripe_t (include/mojette.h): 32 bytes, no padding.
+STRIPE_DTYPE = np.dtype([("plan", "<u8"), ("op", "<i4"), ("erasure_mask", "<u4"),
+                         ("src", "<u8"), ("dst", "<u8")])
+assert STRIPE_DTYPE.itemsize == 32
+
+
+def stripe_table(plans, plan_index, op, erasure_mask, src, dst) -> np.ndarray:
+    """A mojette_stripe_t array: stripe k uses plans[plan_index[k]], operation
+    op[k], erasure_mask[k] and the device addresses src[k], dst[k] (integer
+    arrays, or scalars broadcast over the stripes)."""
+    plan_index = np.asarray(plan_index, dtype=np.int64)
+    handles = np.array([pl.handle for pl in plans], dtype=np.uint64)
+    t = np.zeros(len(plan_index), dtype=STRIPE_DTYPE)
+    t["plan"] = handles[plan_index]
+    t["op"] = op
+    t["erasure_mask"] = np.asarray(erasure_mask, dtype=np.int64).astype(np.uint32)
+    t["src"] = np.asarray(src, dtype=np.uint64)
+    t["dst"] = np.asarray(dst, dtype=np.uint64)
+    return t
+
+
+class Batch:
+    """Owns a ``mojette_batch_t``; keeps the plans it uses alive."""
+
+    def __init__(self, table: np.ndarray, plans, flags: int = 0):
+        table = np.ascontiguousarray(table, dtype=STRIPE_DTYPE)
+        self.plans = list(plans)
+        h = _PTR()
+        _check(lib().mojette_batch_create(table.ctypes.data if len(table) else None, len(table),
+                                          int(flags), ctypes.byref(h)), "mojette_batch_create")
+        self.handle = h.value
+        self._lib = lib()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.mojette_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mojette_batch_create(table: np.ndarray, plans, flags: int = 0) -> Batch:
+    """Build a batch from a stripe_table (``plans``: the Plan objects it uses)."""
+    return Batch(table, plans, flags)
+
+
+def mojette_batch_update(batch: Batch, table: np.ndarray, plans=None, stream=None) -> None:
+    table = np.ascontiguousarray(table, dtype=STRIPE_DTYPE)
+    if plans is not None:
+        batch.plans = list(plans)
+    _check(lib().mojette_batch_update(batch.handle, table.ctypes.data if len(table) else None,
+                                      len(table), _stream(stream)), "mojette_batch_update")
+
+
+def mojette_batch_run(batch: Batch, stream=None) -> None:
+    _check(lib().mojette_batch_run(batch.handle, _stream(stream)), "mojette_batch_run")
+
+
+def mojette_batch_tune(batch: Batch, stream=None, reps: int = 3) -> None:
+    _check(lib().mojette_batch_tune(batch.handle, _stream(stream), int(reps)), "mojette_batch_tune")
+
+
+def mojette_batch_info(batch: Batch) -> dict:
+    launches, groups, work = _I64(), _I64(), _I64()
+    _check(lib().mojette_batch_info(batch.handle, ctypes.byref(launches), ctypes.byref(groups),
+                                    ctypes.byref(work), None), "mojette_batch_info")
+    cfg = (ctypes.c_int32 * (6 * max(1, launches.value)))()
+    _check(lib().mojette_batch_info(batch.handle, None, None, None, cfg), "mojette_batch_info")
+    names = ("op", "Q", "P", "kernel", "param", "flags")
+    configs = [dict(zip(names, cfg[6 * i: 6 * i + 6])) for i in range(launches.value)]
+    return {"launches": int(launches.value), "groups": int(groups.value),
+            "work_items": int(work.value), "configs": configs}
+
+
+def mojette_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+# ---- request server -------------------------------------------------------
+
+# Layouts of mojette_request_t (56 bytes) and mojette_completion_t (40 bytes).
+REQUEST_DTYPE = np.dtype([("id", "<u8"), ("plan", "<u8"), ("op", "<i4"), ("erasure_mask", "<u4"),
+                          ("stripes", "<i8"), ("host_src", "<u8"), ("host_dst", "<u8"),
+                          ("arrival_s", "<f8")])
+COMPLETION_DTYPE = np.dtype([("id", "<u8"), ("status", "<i4"), ("_pad", "<i4"), ("arrival_s", "<f8"),
+                             ("admit_s", "<f8"), ("done_s", "<f8")])
+assert REQUEST_DTYPE.itemsize == 56 and COMPLETION_DTYPE.itemsize == 40
+
+
+class Server:
+    """Owns a ``mojette_server_t``."""
+
+    def __init__(self, budget_bytes: int, slots: int = 3, max_wave_stripes: int = 65536):
+        h = _PTR()
+        _check(lib().mojette_server_create(int(budget_bytes), int(slots), int(max_wave_stripes),
+                                           ctypes.byref(h)), "mojette_server_create")
+        self.handle = h.value
+        self._lib = lib()
+        self._buf = np.zeros(4096, dtype=COMPLETION_DTYPE)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.mojette_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mojette_server_create(budget_bytes: int, slots: int = 3, max_wave_stripes: int = 65536) -> Server:
+    return Server(budget_bytes, slots, max_wave_stripes)
+
+
+def mojette_server_submit(server: Server, reqs: np.ndarray) -> None:
+    reqs = np.ascontiguousarray(reqs, dtype=REQUEST_DTYPE)
+    _check(lib().mojette_server_submit(server.handle, reqs.ctypes.data if len(reqs) else None, len(reqs)),
+           "mojette_server_submit")
+
+
+def mojette_server_poll(server: Server) -> np.ndarray:
+    """Progress, then every completion available (a COMPLETION_DTYPE array)."""
+    out = []
+    n = _I64()
+    while True:
+        code = lib().mojette_server_poll(server.handle, server._buf.ctypes.data, len(server._buf),
+                                         ctypes.byref(n))
+        out.append(server._buf[: n.value].copy())
+        _check(code, "mojette_server_poll")
+        if n.value < len(server._buf):
+            break
+    return np.concatenate(out)
+
+
+def mojette_server_now(server: Server) -> float:
+    t = ctypes.c_double()
+    _check(lib().mojette_server_now(server.handle, ctypes.byref(t)), "mojette_server_now")
+    return t.value
+
+
+def mojette_server_stats(server: Server) -> dict:
+    v = [_I64() for _ in range(6)]
+    _check(lib().mojette_server_stats(server.handle, *[ctypes.byref(x) for x in v]), "mojette_server_stats")
+    names = ("queued", "in_flight", "waves", "completed", "pool_used", "pool_peak")
+    return {k: int(x.value) for k, x in zip(names, v)}
+
+
+def mojette_server_destroy(server: Server) -> None:
+    server.close()
 
 
 def mojette_device_status(clear: bool = True) -> int:

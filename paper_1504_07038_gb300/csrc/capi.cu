@@ -116,7 +116,7 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
     if (!aligned16(d_img) || !aligned16(d_proj)) return -ERANGE;
     Plan *pl = reinterpret_cast<Plan *>(plan);
     int err = 0;
-    EncodeArgs a;
+    EncodeArgs a{};
     a.img = d_img;
     a.proj = d_proj;
     a.S = S;
@@ -166,6 +166,11 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
         a.srcL[l] = sc->srcL[l];
         a.srcR[l] = sc->srcR[l];
     }
+    a.chunk_w = sc->chunk_w;
+    for (int c = 0; c < kStreamChunks; ++c) {
+        a.chunk_wait[c] = sc->chunk_wait[c];
+        a.chunk_done[c] = sc->chunk_done[c];
+    }
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
@@ -203,6 +208,11 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
         a.split[l] = sc->split[l];
         a.srcL[l] = sc->srcL[l];
         a.srcR[l] = sc->srcR[l];
+    }
+    a.chunk_w = sc->chunk_w;
+    for (int c = 0; c < kStreamChunks; ++c) {
+        a.chunk_wait[c] = sc->chunk_wait[c];
+        a.chunk_done[c] = sc->chunk_done[c];
     }
     a.status = device_status_ptr(&err);
     if (err) return err;

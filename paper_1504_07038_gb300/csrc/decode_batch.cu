@@ -1,0 +1,25 @@
+// Batched decode launcher: work items of G stripes, each with its own
+// reconstruction path (DecGroup) and per-stripe addresses, in one launch
+// (the kernels are in decode_kernels.cuh; the tables are built by batch.cpp).
+#include "decode_kernels.cuh"
+
+namespace mojette {
+
+int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaStream_t st)
+{
+    DecodeLayout L;
+    int err = decode_layout(b.P, b.Q, b.maxp, b.maxT, cfg, &L);
+    if (err) return err;
+    DecParams a;
+    std::memset(&a, 0, sizeof(a));
+    a.groups = b.groups;
+    a.work = b.work;
+    a.nwork = b.nwork;
+    a.srcp = b.srcp;
+    a.dstp = b.dstp;
+    a.P = b.P;
+    a.Q = b.Q;
+    return launch_decode_kernel<true>(a, L, cfg, b.nwork, st);
+}
+
+}  // namespace mojette

@@ -1,0 +1,821 @@
+// Inverse Mojette transform (decode) kernels, Sec. 2.2, along a
+// pre-determined reconstruction path (one projection dedicated to each line,
+// swept from both ends of the line; the path itself is built on the host,
+// plan.cpp).
+//
+// Every pixel (l, x) is rebuilt in gather form: the bin of its dedicated
+// projection (direction p) XOR the other pixels of that bin's discrete line,
+// (l', x + (l' - l) p) for l' != l inside the image. The schedule
+// guarantees those are known when the pixel is rebuilt, so the result is
+// the value the paper's "subtract its contribution from all projections"
+// procedure reaches, with at most Q - 1 XORs per pixel (Sec. 3).
+//
+// GB300 design. Decode is HBM-bound in bytes but carries a sequential
+// dependency along the lines (about P/2 steps per stripe with two fronts),
+// so the kernels are built to keep that chain short and many stripes in
+// flight:
+//   - the pixel line l+1 rebuilt in the same step is forwarded in a
+//     register, so the only shared-memory round trip on the critical path
+//     is one per step;
+//   - the 64-bit words of the G stripes of a warp are interleaved in shared
+//     memory (word = column * stride + stripe), so lanes that run the same
+//     front of different stripes read one contiguous run: no bank conflicts;
+//   - the Q*P bins the path uses are staged in pixel order by 8-byte
+//     cp.async copies (coalesced; the descending bin order costs nothing)
+//     and each rebuilt pixel overwrites its own bin, so a stripe needs Q*P
+//     words of shared memory plus zero columns around the rows;
+//   - the zero columns stand for pixels outside the image (the XOR
+//     identity), so no bounds test sits in the inner loop.
+//
+// Every kernel comes in two forms: plain (one reconstruction path, stripes
+// back to back at fixed strides) and batched (work items of G stripes, each
+// with its own path from a device table, stripes anywhere in memory through
+// per-stripe address arrays). Both run the same instructions per step.
+#pragma once
+
+#include <algorithm>
+#include <cerrno>
+#include <cstdlib>
+#include <cstring>
+
+#include "ptx.cuh"
+
+namespace mojette {
+namespace {
+
+struct DecParams {
+    // plain form
+    const uint64_t *proj;   // stripe s at proj + s * total
+    uint64_t *img;          // stripe s at img + s * Q * P
+    int64_t S;
+    DecGroup grp;           // its reconstruction path
+    // batched form
+    const DecGroup *groups;
+    const DecWork *work;
+    int64_t nwork;
+    const uint64_t *const *srcp;
+    uint64_t *const *dstp;
+    // layout (both forms)
+    int64_t total;
+    int P, Q;
+    int reach;    // zero columns before, between and after the rows of a stripe
+    int RP;       // row pitch in columns: P + reach
+    int G;        // stripes per work item (one warp)
+    int GS;       // interleave stride (decode_lines: G; decode_fronts: G rounded to odd)
+    int TS;       // words per step table in shared memory
+    int gpc;      // work items per CTA (one warp per CTA)
+    int persist;  // 1: grid-stride over chunks of gpc items
+    int steady;   // decode_fronts: 1 to run steady steps on the short path
+};
+
+__device__ __forceinline__ uint64_t ld_s64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+// Load when `pred` is nonzero, else 0.
+__device__ __forceinline__ uint64_t ld_s64_if(uint32_t addr, uint32_t pred)
+{
+    uint64_t v;
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\tmov.b64 %0, 0;\n\t"
+                 "@p ld.shared.u64 %0, [%1];\n\t}"
+                 : "=l"(v) : "r"(addr), "r"(pred));
+    return v;
+}
+
+__device__ __forceinline__ void st_s64(uint32_t addr, uint64_t v)
+{
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(addr), "l"(v));
+}
+
+// Store when `pred` is nonzero.
+__device__ __forceinline__ void st_s64_if(uint32_t addr, uint64_t v, uint32_t pred)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.shared.u64 [%0], %1;\n\t}"
+                 ::"r"(addr), "l"(v), "r"(pred));
+}
+
+// Walks the work items of one CTA: `body(item)` for item = base + k,
+// k < gpc, base = blockIdx.x * gpc (+ gridDim.x * gpc when persistent).
+template <typename F>
+__device__ __forceinline__ void for_items(const DecParams &a, int64_t nitems, F &&body)
+{
+    const int64_t stride = a.persist ? (int64_t)gridDim.x * a.gpc : nitems;
+    for (int64_t base = (int64_t)blockIdx.x * a.gpc; base < nitems; base += stride)
+        for (int k = 0; k < a.gpc; ++k) {
+            const int64_t item = base + k;
+            if (item >= nitems) break;
+            body(item);
+        }
+}
+
+// ---------------------------------------------------------------------------
+// decode_fronts: one lane runs one front (left or right) of one stripe, all Q
+// lines, visiting the lines from Q-1 down to 0 each step. Lanes 0..15 are
+// left fronts and 16..31 right fronts of the same G stripes.
+// QT: number of lines at compile time (0: any Q up to kMaxLines, slower).
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32) decode_fronts(const __grid_constant__ DecParams a)
+{
+    constexpr int QA = QT ? QT : kMaxLines;   // register array extent
+    extern __shared__ __align__(16) uint64_t sm[];
+    const int Q = QT ? QT : a.Q;
+    const int P = a.P, G = a.G, GS = a.GS;
+    const int lane = threadIdx.x & 31;
+    // Step words first, then the stripe slots; word (column c, slot g) sits
+    // at c * GS + g.
+    uint32_t *steps = reinterpret_cast<uint32_t *>(sm);
+    uint64_t *wbuf = sm + a.TS / 2;
+    // Zero columns stand for pixels outside the image (the XOR identity):
+    // the reach columns before each row and after the last one. Rows are
+    // always staged before they are read.
+    for (int ll = 0; ll <= Q; ++ll)
+        for (int i = lane; i < a.reach * GS; i += 32) wbuf[ll * a.RP * GS + i] = 0;
+    const uint32_t wbase = smem_addr(wbuf);
+
+    // Front lanes: lane = 16 * side + g. Lanes past G shadow stripe slot 0:
+    // they load the same words and store the same values as lane g = 0 of
+    // their side, so every lane runs the same instructions.
+    const int side = lane >> 4;
+    const int graw = lane & 15;
+    const int g = graw < G ? graw : 0;
+    const int stepb = (side ? -1 : 1) * GS * 8;
+
+    // Per line: start address of this front's pixel, the bit of the step word
+    // that moves it, whether a steady step forwards its line l+1 operand, and
+    // the byte offsets from it to the other pixels of its bin line,
+    // (l2, x + (l2 - l) p) -- the last three depend on the path.
+    uint32_t start[QA], bit[QA], keep[QA];
+    uint64_t fmask[QA];
+    int dl[QA][QA];
+#pragma unroll
+    for (int l = 0; l < QA; ++l) {
+        if (l >= Q) break;
+        start[l] = wbase + ((a.reach + l * a.RP + (side ? P - 1 : 0)) * GS + g) * 8;
+        bit[l] = 1u << (2 * l + side);
+    }
+    int T4 = 0;
+    auto load_group = [&](const DecGroup &gr) {
+        const int T = gr.T;
+        T4 = (T + 3) & ~3;
+        for (int t = lane; t < T4; t += 32) steps[t] = t < T ? gr.steps[t] : 0u;
+#pragma unroll
+        for (int l = 0; l < QA; ++l) {
+            if (l >= Q) break;
+            const int p = gr.p[2 * l + side];
+            const uint32_t f = (l + 1 < Q) ? (gr.fwd >> (2 * l + side)) & 1u : 0u;
+            keep[l] = f ^ 1u;
+            fmask[l] = f ? ~0ull : 0ull;
+#pragma unroll
+            for (int l2 = 0; l2 < QA; ++l2) {
+                if (l2 >= Q) break;
+                dl[l][l2] = (l2 - l) * (a.RP + p) * GS * 8;
+            }
+        }
+    };
+    const DecGroup *gp = nullptr;   // batched: the current work item's path
+    auto grp = [&]() -> const DecGroup & {
+        if constexpr (BATCHED) return *gp;
+        else return a.grp;
+    };
+    if constexpr (!BATCHED) load_group(a.grp);
+    __syncwarp();
+
+    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes.
+    const int XK = 32 / G;
+    const int xk = lane / G, gg = lane - xk * G;
+    const bool copy_ok = xk < XK;
+
+    int cur = -1;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            nst = wk.nst;
+            first = wk.first;
+            if (wk.group != cur) {
+                cur = wk.group;
+                gp = a.groups + cur;
+                __syncwarp();
+                load_group(*gp);
+                __syncwarp();
+            }
+        } else {
+            s0 = item * G;
+            nst = (int)min64(G, a.S - s0);
+        }
+
+        // stage the Q*P bins the path uses, in pixel order
+        if (copy_ok && gg < nst) {
+            const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+            for (int ll = 0; ll < Q; ++ll) {
+                const int sp = grp().split[ll];
+                const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
+                uint64_t *dst = wbuf + (a.reach + ll * a.RP) * GS + gg;
+                for (int x = xk; x < P; x += XK)
+                    cp_async8(dst + x * GS, src + ((x < sp ? sl : sr) - x));
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+
+        // replay the path
+        uint32_t pos[QA];
+#pragma unroll
+        for (int l = 0; l < QA; ++l)
+            if (l < Q) pos[l] = start[l];
+
+        // Steady step: every line moves; line l's operand on line l+1 is the
+        // pixel rebuilt just before in this step exactly where fwd says so.
+        auto steady = [&]() {
+            uint64_t v[QA], own[QA], op[QA][QA];
+#pragma unroll
+            for (int l = QA - 1; l >= 0; --l) {
+                if (l >= Q) continue;
+                own[l] = ld_s64(pos[l]);
+#pragma unroll
+                for (int l2 = 0; l2 < QA; ++l2) {
+                    if (l2 >= Q || l2 == l) continue;
+                    if (l2 == l + 1) op[l][l2] = ld_s64_if(pos[l] + dl[l][l2], keep[l]);
+                    else op[l][l2] = ld_s64(pos[l] + dl[l][l2]);
+                }
+            }
+#pragma unroll
+            for (int l = QA - 1; l >= 0; --l) {
+                if (l >= Q) continue;
+                uint64_t acc = own[l];
+#pragma unroll
+                for (int l2 = 0; l2 < QA; ++l2)
+                    if (l2 < Q && l2 != l) acc ^= op[l][l2];
+                if (l + 1 < Q) acc ^= v[l + 1] & fmask[l];
+                v[l] = acc;
+            }
+#pragma unroll
+            for (int l = 0; l < QA; ++l) {
+                if (l >= Q) break;
+                st_s64(pos[l], v[l]);
+                pos[l] += stepb;
+            }
+            __syncwarp();
+        };
+        // Any step: per-line activity bits, forwarding where line l+1 moved
+        // onto exactly the operand's pixel in this step.
+        auto general = [&](uint32_t w) {
+            uint64_t own[QA], op[QA][QA], v[QA];
+            uint32_t act[QA];
+#pragma unroll
+            for (int l = QA - 1; l >= 0; --l) {
+                if (l >= Q) continue;
+                own[l] = ld_s64(pos[l]);
+#pragma unroll
+                for (int l2 = 0; l2 < QA; ++l2) {
+                    if (l2 >= Q || l2 == l) continue;
+                    op[l][l2] = ld_s64(pos[l] + dl[l][l2]);
+                }
+            }
+#pragma unroll
+            for (int l = QA - 1; l >= 0; --l) {
+                if (l >= Q) continue;
+                act[l] = w & bit[l];
+                uint64_t acc = own[l];
+#pragma unroll
+                for (int l2 = 0; l2 < QA; ++l2) {
+                    if (l2 >= Q || l2 == l) continue;
+                    uint64_t o = op[l][l2];
+                    if (l2 == l + 1 && act[l2] && pos[l2] == pos[l] + dl[l][l2]) o = v[l2];
+                    acc ^= o;
+                }
+                v[l] = acc;
+            }
+#pragma unroll
+            for (int l = 0; l < QA; ++l) {
+                if (l >= Q) break;
+                st_s64_if(pos[l], v[l], act[l]);
+                pos[l] += act[l] ? stepb : 0;
+            }
+            __syncwarp();
+        };
+        const uint32_t steady_bit = (QT && QT <= kFastMaxLines && a.steady) ? kStepSteady : 0u;
+        for (int t = 0; t < T4; ++t) {
+            const uint32_t w = steps[t];
+            if (w & steady_bit) steady();
+            else general(w);
+        }
+
+        // write the rebuilt image
+        if (copy_ok && gg < nst) {
+            uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+            for (int ll = 0; ll < Q; ++ll) {
+                const uint64_t *buf = wbuf + (a.reach + ll * a.RP) * GS + gg;
+                for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * GS]);
+            }
+        }
+        __syncwarp();
+    });
+}
+
+// ---------------------------------------------------------------------------
+// decode_lines: one lane per (stripe, line, front). A warp holds G = 32/(2Q)
+// stripes; at every step each lane rebuilds the next pixel of its line's
+// front (when the step word moves it), from its staged bin and the other
+// pixels of the bin line read from shared memory -- except the operand on
+// line l+1, which line l+1 may rebuild in this same step. Those same-step
+// links (bit 2l+side of the step's forward word) form chains l -> l+1 -> ...
+// within a front; the chain values are a segmented suffix XOR over the lines,
+// done with log2(Q) rounds of warp shuffles, so every lane of every line
+// works at every step and a step costs one shared-memory round trip.
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    const int P = a.P, G = a.G;
+    const int lane = threadIdx.x & 31;
+    // step words, forward words (TS words each), then the slots
+    uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
+    uint32_t *fwdw = stepw + a.TS;
+    uint64_t *wbuf = sm + a.TS;
+    for (int ll = 0; ll <= Q; ++ll)
+        for (int i = lane; i < a.reach * G; i += 32) wbuf[ll * a.RP * G + i] = 0;
+    const uint32_t wbase = smem_addr(wbuf);
+
+    // Rebuild lanes: lane = (2l + side) * G + g; lanes past 2Q*G shadow lane 0.
+    const int lsr = lane / G;
+    const bool ok = lsr < 2 * Q;
+    const int ls = ok ? lsr : 0;
+    const int g = ok ? lane - lsr * G : 0;
+    const int l = ls >> 1, side = ls & 1;
+    const uint32_t bitmask = ok ? 1u << ls : 0u;   // shadow lanes never store
+    const uint32_t start = wbase + ((a.reach + l * a.RP + (side ? P - 1 : 0)) * G + g) * 8;
+    const int stepb = (side ? -1 : 1) * G * 8;
+    const uint32_t has_next = (l + 1 < Q) ? 1u : 0u;
+
+    // Path-dependent state. The operands of line l sit on lines
+    // l2 = l+1+k (mod Q), k = 0 .. Q-2. k = 0 is line l+1, which may be
+    // forwarded, except for l = Q-1 where it wraps to line 0 and is always
+    // read. For steady steps: this lane's link (line l forwards from line
+    // l+1) and the link state after each scan round, from the path's steady
+    // pattern: after the round with stride d, line l is still linked iff it
+    // was, and line l+d was too.
+    int T4 = 0, d0 = 0;
+    int dk[Q > 2 ? Q - 2 : 1];
+    uint32_t sfw = 0u;
+    uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    auto load_group = [&](const DecGroup &gr) {
+        const int T = gr.T;
+        T4 = (T + 3) & ~3;
+        for (int t = lane; t < T4; t += 32) {
+            stepw[t] = t < T ? gr.steps[t] : 0u;
+            fwdw[t] = t < T ? gr.steps[T + t] : 0u;
+        }
+        const int p = gr.p[ls];
+        const int colstep = (a.RP + p) * G * 8;   // bytes from line l to line l+1 on a bin line
+        d0 = (has_next ? 1 : 1 - Q) * colstep;
+#pragma unroll
+        for (int k = 1; k < Q - 1; ++k) {
+            const int l2 = (l + 1 + k) % Q;
+            dk[k - 1] = (l2 - l) * colstep;
+        }
+        sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
+        uint32_t c[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
+#pragma unroll
+        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+            slink[r] = ok ? c[l] : 0u;
+            uint32_t nc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+        }
+    };
+    const DecGroup *gp = nullptr;   // batched: the current work item's path
+    auto grp = [&]() -> const DecGroup & {
+        if constexpr (BATCHED) return *gp;
+        else return a.grp;
+    };
+    if constexpr (!BATCHED) load_group(a.grp);
+    __syncwarp();
+
+    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes.
+    const int XK = 32 / G;
+    const int xk = lane / G, gg = lane - xk * G;
+    const bool copy_ok = xk < XK;
+
+    int cur = -1;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            nst = wk.nst;
+            first = wk.first;
+            if (wk.group != cur) {
+                cur = wk.group;
+                gp = a.groups + cur;
+                __syncwarp();
+                load_group(*gp);
+                __syncwarp();
+            }
+        } else {
+            s0 = item * G;
+            nst = (int)min64(G, a.S - s0);
+        }
+
+        if (copy_ok && gg < nst) {
+            const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+            for (int ll = 0; ll < Q; ++ll) {
+                const int sp = grp().split[ll];
+                const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
+                uint64_t *dst = wbuf + (a.reach + ll * a.RP) * G + gg;
+                for (int x = xk; x < P; x += XK)
+                    cp_async8(dst + x * G, src + ((x < sp ? sl : sr) - x));
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+
+        uint32_t pos = start;
+        for (int t = 0; t < T4; ++t) {
+            const uint32_t w = stepw[t];
+            if (w & kStepSteady) {
+                // steady: every line moves, links are the path's pattern
+                uint64_t v = ld_s64(pos);
+#pragma unroll
+                for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
+                if (Q > 1) v ^= ld_s64_if(pos + d0, (sfw & has_next) ^ 1u);
+#pragma unroll
+                for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                    if (slink[r]) v ^= tv;
+                }
+                st_s64_if(pos, v, ok);
+                pos += stepb;
+                __syncwarp();
+                continue;
+            }
+            const uint32_t f = fwdw[t];
+            const uint32_t act = w & bitmask;
+            const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
+            uint64_t v = ld_s64(pos);
+#pragma unroll
+            for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
+            if (Q > 1) v ^= ld_s64_if(pos + d0, (fw & has_next) ^ 1u);
+            // segmented suffix XOR: v_l ^= v_{l+1} while linked
+            uint32_t c = fw;
+#pragma unroll
+            for (int d = 1; d < Q; d <<= 1) {
+                const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                const uint32_t tc = __shfl_down_sync(0xffffffffu, c, 2 * d * G);
+                if (c) {
+                    v ^= tv;
+                    c = tc;
+                }
+            }
+            st_s64_if(pos, v, act);
+            pos += act ? stepb : 0;
+            __syncwarp();
+        }
+
+        if (copy_ok && gg < nst) {
+            uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+            for (int ll = 0; ll < Q; ++ll) {
+                const uint64_t *buf = wbuf + (a.reach + ll * a.RP) * G + gg;
+                for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * G]);
+            }
+        }
+        __syncwarp();
+    });
+}
+
+// ---------------------------------------------------------------------------
+// decode_stream: decode_lines' lanes and steps, with the stripe streamed
+// through shared memory instead of staged and written whole:
+//   - rows are packed at pitch RP (no zero columns between them); an operand
+//     outside the image reads one zero column instead, chosen per operand
+//     from the front's column, so a stripe takes Q*P words of shared memory
+//     and more stripes fit on an SM;
+//   - the bins arrive in kStreamChunks cp.async groups ordered by distance
+//     from the ends where the fronts start; the step loop waits for chunk c
+//     only before the first step that reaches it, so later chunks land
+//     while the first ones are being rebuilt;
+//   - each chunk goes back to global memory as soon as its last pixel is
+//     rebuilt, so the write-out overlaps the remaining steps.
+// The chunk steps come with the path (Schedule::chunk_wait, chunk_done).
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32) decode_stream(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    constexpr int NC = kStreamChunks;
+    const int P = a.P, G = a.G, RP = a.RP;
+    const int lane = threadIdx.x & 31;
+    uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
+    uint32_t *fwdw = stepw + a.TS;
+    uint64_t *wbuf = sm + a.TS;
+    // the zero column after the rows
+    if (lane < G) wbuf[(size_t)Q * RP * G + lane] = 0;
+    const uint32_t wbase = smem_addr(wbuf);
+
+    // Rebuild lanes: lane = (2l + side) * G + g; lanes past 2Q*G shadow lane 0.
+    const int lsr = lane / G;
+    const bool ok = lsr < 2 * Q;
+    const int ls = ok ? lsr : 0;
+    const int g = ok ? lane - lsr * G : 0;
+    const int l = ls >> 1, side = ls & 1;
+    const uint32_t bitmask = ok ? 1u << ls : 0u;
+    const uint32_t start = wbase + ((l * RP + (side ? P - 1 : 0)) * G + g) * 8;
+    const uint32_t zaddr = wbase + ((Q * RP) * G + g) * 8;
+    const int stepb = (side ? -1 : 1) * G * 8;
+    const int dir = side ? -1 : 1;
+    const uint32_t has_next = (l + 1 < Q) ? 1u : 0u;
+
+    // Path-dependent state: for the operands on lines l2 = l+1+k (mod Q),
+    // k = 0 .. Q-2, the column offset (l2 - l) p and the byte offset from
+    // this lane's pixel; slink / sfw as in decode_lines.
+    int T4 = 0;
+    int ecol[Q > 1 ? Q - 1 : 1], eoff[Q > 1 ? Q - 1 : 1];
+    uint32_t sfw = 0u;
+    uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    int cw = 1, cwait[NC], cdone[NC];
+    auto load_group = [&](const DecGroup &gr) {
+        const int T = gr.T;
+        T4 = (T + 3) & ~3;
+        for (int t = lane; t < T4; t += 32) {
+            stepw[t] = t < T ? gr.steps[t] : 0u;
+            fwdw[t] = t < T ? gr.steps[T + t] : 0u;
+        }
+        const int p = gr.p[ls];
+#pragma unroll
+        for (int k = 0; k < Q - 1; ++k) {
+            const int l2 = (l + 1 + k) % Q;
+            ecol[k] = (l2 - l) * p;
+            eoff[k] = (l2 - l) * (RP + p) * G * 8;
+        }
+        sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
+        uint32_t c[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
+#pragma unroll
+        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+            slink[r] = ok ? c[l] : 0u;
+            uint32_t nc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+        }
+        cw = gr.chunk_w;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            cwait[q] = gr.chunk_wait[q];
+            cdone[q] = gr.chunk_done[q];
+        }
+    };
+    const DecGroup *gp = nullptr;
+    auto grp = [&]() -> const DecGroup & {
+        if constexpr (BATCHED) return *gp;
+        else return a.grp;
+    };
+    if constexpr (!BATCHED) load_group(a.grp);
+    __syncwarp();
+
+    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes.
+    const int XK = 32 / G;
+    const int xk = lane / G, gg = lane - xk * G;
+    const bool copy_ok = xk < XK;
+
+    // Columns of chunk q on line ll: the left front's x in [d0, min(d1, sp))
+    // and the right front's x = P-1-d, d in [d0, min(d1, P - sp)).
+    auto chunk_cols = [&](int q, int ll, auto &&fn) {
+        const int d0 = q * cw, d1 = (q == NC - 1) ? P : (q + 1) * cw;
+        const int sp = grp().split[ll];
+        const int eL = min(d1, sp), eR = min(d1, P - sp);
+        for (int x = d0 + xk; x < eL; x += XK) fn(x, 0);
+        for (int d = d0 + xk; d < eR; d += XK) fn(P - 1 - d, 1);
+    };
+
+    int cur = -1;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            nst = wk.nst;
+            first = wk.first;
+            if (wk.group != cur) {
+                cur = wk.group;
+                gp = a.groups + cur;
+                __syncwarp();
+                load_group(*gp);
+                __syncwarp();
+            }
+        } else {
+            s0 = item * G;
+            nst = (int)min64(G, a.S - s0);
+        }
+        const bool mine = copy_ok && gg < nst;
+        const uint64_t *src = nullptr;
+        uint64_t *out = nullptr;
+        if (mine) {
+            src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+            out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+        }
+
+        // stage: one cp.async group per chunk (empty groups for idle lanes)
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            if (mine)
+                for (int ll = 0; ll < Q; ++ll) {
+                    const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
+                    uint64_t *dst = wbuf + (size_t)ll * RP * G + gg;
+                    chunk_cols(q, ll, [&](int x, int right) {
+                        cp_async8(dst + x * G, src + ((right ? sr : sl) - x));
+                    });
+                }
+            cp_async_commit();
+        }
+        // write chunk q of every line back
+        auto put = [&](int q) {
+            if (mine)
+                for (int ll = 0; ll < Q; ++ll) {
+                    const uint64_t *buf = wbuf + (size_t)ll * RP * G + gg;
+                    chunk_cols(q, ll, [&](int x, int) { __stcs(out + ll * P + x, buf[x * G]); });
+                }
+        };
+        auto wait_chunk = [&](int q) {
+            switch (q) {
+            case 0: cp_async_wait_group<NC - 1>(); break;
+            case 1: cp_async_wait_group<NC - 2 < 0 ? 0 : NC - 2>(); break;
+            case 2: cp_async_wait_group<NC - 3 < 0 ? 0 : NC - 3>(); break;
+            default: cp_async_wait_all(); break;
+            }
+            __syncwarp();
+        };
+
+        // chunk q's wait / done step, kept in registers (constant indices only)
+        auto chunk_step = [&](const int (&tab)[NC], int q) {
+            int v = 0x7fffffff;
+#pragma unroll
+            for (int i = 0; i < NC; ++i) v = (i == q) ? tab[i] : v;
+            return v;
+        };
+        uint32_t pos = start;
+        int x = side ? P - 1 : 0;   // this lane's front column
+        int ev = 0, ov = 0;
+        int next_wait = cwait[0], next_done = cdone[0];
+        // operand address: its pixel, or the zero column outside the image
+        auto opaddr = [&](int k) -> uint32_t {
+            return (unsigned)(x + ecol[k]) < (unsigned)P ? pos + eoff[k] : zaddr;
+        };
+        for (int t = 0; t < T4; ++t) {
+            while (t >= next_wait) {
+                wait_chunk(ev++);
+                next_wait = chunk_step(cwait, ev);
+            }
+            const uint32_t w = stepw[t];
+            const bool steady = (w & kStepSteady) != 0;
+            const uint32_t f = steady ? 0u : fwdw[t];
+            const uint32_t fw = steady ? sfw : (ok ? (f >> ls) & 1u : 0u);
+            uint64_t v = ld_s64(pos);
+#pragma unroll
+            for (int k = 1; k < Q - 1; ++k) v ^= ld_s64(opaddr(k));
+            if (Q > 1) {
+                const uint32_t a0 = opaddr(0);
+                v ^= ld_s64_if(a0, (fw & has_next) ^ 1u);
+            }
+            uint32_t act;
+            if (steady) {
+#pragma unroll
+                for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                    if (slink[r]) v ^= tv;
+                }
+                act = ok ? 1u : 0u;
+            } else {
+                uint32_t c = fw;
+#pragma unroll
+                for (int d = 1; d < Q; d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                    const uint32_t tc = __shfl_down_sync(0xffffffffu, c, 2 * d * G);
+                    if (c) {
+                        v ^= tv;
+                        c = tc;
+                    }
+                }
+                act = w & bitmask;
+            }
+            st_s64_if(pos, v, act);
+            if (act) {
+                pos += stepb;
+                x += dir;
+            }
+            __syncwarp();
+            while (t >= next_done) {
+                put(ov++);
+                next_done = chunk_step(cdone, ov);
+            }
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        while (ov < NC) put(ov++);
+        __syncwarp();
+    });
+}
+
+using DecKernel = void (*)(const DecParams);
+
+template <bool BATCHED>
+DecKernel pick_fronts(int Q)
+{
+    switch (Q) {
+    case 1: return decode_fronts<1, BATCHED>;
+    case 2: return decode_fronts<2, BATCHED>;
+    case 3: return decode_fronts<3, BATCHED>;
+    case 4: return decode_fronts<4, BATCHED>;
+    case 5: return decode_fronts<5, BATCHED>;
+    case 6: return decode_fronts<6, BATCHED>;
+    case 7: return decode_fronts<7, BATCHED>;
+    case 8: return decode_fronts<8, BATCHED>;
+    default: return decode_fronts<0, BATCHED>;
+    }
+}
+
+template <bool BATCHED>
+DecKernel pick_lines(int Q)
+{
+    switch (Q) {
+    case 1: return decode_lines<1, BATCHED>;
+    case 2: return decode_lines<2, BATCHED>;
+    case 3: return decode_lines<3, BATCHED>;
+    case 4: return decode_lines<4, BATCHED>;
+    case 5: return decode_lines<5, BATCHED>;
+    case 6: return decode_lines<6, BATCHED>;
+    case 7: return decode_lines<7, BATCHED>;
+    case 8: return decode_lines<8, BATCHED>;
+    default: return nullptr;
+    }
+}
+
+template <bool BATCHED>
+DecKernel pick_stream(int Q)
+{
+    switch (Q) {
+    case 1: return decode_stream<1, BATCHED>;
+    case 2: return decode_stream<2, BATCHED>;
+    case 3: return decode_stream<3, BATCHED>;
+    case 4: return decode_stream<4, BATCHED>;
+    case 5: return decode_stream<5, BATCHED>;
+    case 6: return decode_stream<6, BATCHED>;
+    case 7: return decode_stream<7, BATCHED>;
+    case 8: return decode_stream<8, BATCHED>;
+    default: return nullptr;
+    }
+}
+
+// Launch a decode kernel over `nitems` work items with a layout from
+// decode_layout; a's path and addressing fields are already set.
+template <bool BATCHED>
+int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig &cfg,
+                         int64_t nitems, cudaStream_t st)
+{
+    a.reach = L.reach;
+    a.RP = L.RP;
+    a.G = L.G;
+    a.GS = L.GS;
+    a.TS = L.TS;
+    a.gpc = std::max(1, cfg.gpc);
+    a.persist = cfg.persist ? 1 : 0;
+    if (const char *e = getenv("MOJETTE_DECODE_STEADY")) a.steady = atoi(e) ? 1 : 0;
+    else a.steady = 1;
+    if (nitems <= 0) return 0;
+    DecKernel fn = L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
+                 : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
+                                 : pick_fronts<BATCHED>(a.Q);
+    if (!fn) return -EINVAL;
+    int err = 0;
+    if ((err = record_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)L.smem))))
+        return err;
+    int64_t grid = (nitems + a.gpc - 1) / a.gpc;
+    if (a.persist) {
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
+        if ((err = record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return err;
+        if ((err = record_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32, (size_t)L.smem))))
+            return err;
+        grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * sms);
+    }
+    fn<<<(unsigned)grid, 32, (size_t)L.smem, st>>>(a);
+    return record_cuda(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace mojette

@@ -25,6 +25,10 @@ constexpr uint32_t kStatusWaitTimeout = 1u;
 constexpr uint32_t kStepSteady = 1u << 31;
 constexpr int kFastMaxLines = 15;
 
+// decode_stream stages and writes a stripe in this many chunks of columns,
+// by distance from the nearer end of each line's front.
+constexpr int kStreamChunks = 4;
+
 // A bounded device-side wait gives up after this many nanoseconds.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
@@ -45,7 +49,30 @@ struct Schedule {
     std::vector<uint32_t> steps;     // T words, 2 bits per line
     std::vector<uint32_t> fwdw;      // T words: bit 2l+side set when line l of that
                                      // front uses line l+1's pixel of the same step
+    // Chunks of a stripe for streamed staging and output: pixel (l, x) is in
+    // chunk min(d / chunk_w, kStreamChunks - 1), d its distance from the end
+    // its front starts at (x left of split[l], else P - 1 - x). Chunk c must
+    // be staged before step chunk_wait[c] (non-decreasing, [0] = 0) and is
+    // final after step chunk_done[c] (non-decreasing).
+    int32_t chunk_w = 1;
+    int32_t chunk_wait[kStreamChunks] = {};
+    int32_t chunk_done[kStreamChunks] = {};
     std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
+};
+
+// Launch configuration of the decode kernels (chosen by the autotuner for a
+// batch, else the defaults here).
+struct DecodeConfig {
+    int kernel = 0;    // 0: decode_lines (Q <= 8), 1: decode_fronts, 2: decode_stream (Q <= 8)
+    int gpc = 4;       // work items (groups of G stripes) per CTA
+    int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
+    int spread = 0;    // decode_lines: 1 to pad the row pitch so that the lines of
+                       // a warp fall on different shared-memory banks
+};
+
+// Launch configuration of the encode kernel.
+struct EncodeConfig {
+    int tile_bytes = 0;   // target bytes of a tile of stripes; 0: by Q
 };
 
 struct Plan {
@@ -57,6 +84,10 @@ struct Plan {
     int64_t total = 0;
     std::mutex mu;
     std::map<uint32_t, std::unique_ptr<Schedule>> schedules;
+    // autotuned configurations (batch.cpp); used by batches of this plan
+    bool tuned_dec = false, tuned_enc = false;
+    DecodeConfig dec_cfg;
+    EncodeConfig enc_cfg;
 };
 
 // ---- host helpers (plan.cpp) ---------------------------------------------
@@ -70,8 +101,11 @@ uint32_t *device_status_ptr(int *err);  // per-device status word
 
 // ---- kernel launchers -------------------------------------------------------
 struct EncodeArgs {
-    const uint64_t *img;
-    uint64_t *proj;
+    const uint64_t *img;            // plain: stripe s at img + s * Q * P
+    uint64_t *proj;                 // plain: stripe s at proj + s * total
+    const uint64_t *const *srcp;    // batched: stripe s at srcp[s] (device array)
+    uint64_t *const *dstp;          //   and its bins at dstp[s]
+    int tile_bytes;                 // 0: by Q
     int64_t S;
     int64_t total;
     int P, Q, n;
@@ -80,7 +114,8 @@ struct EncodeArgs {
     int64_t bmin[kMaxProj];
     uint32_t *status;
 };
-int launch_encode(const EncodeArgs &a, cudaStream_t stream);
+int launch_encode(const EncodeArgs &a, cudaStream_t stream);           // img/proj
+int launch_encode_batched(const EncodeArgs &a, cudaStream_t stream);   // srcp/dstp
 
 struct DecodeArgs {
     const uint64_t *proj;
@@ -93,9 +128,54 @@ struct DecodeArgs {
     uint32_t fwd;                   // operand pattern of the steady steps
     int32_t pL[kMaxLines], pR[kMaxLines], split[kMaxLines];
     int64_t srcL[kMaxLines], srcR[kMaxLines];
+    int32_t chunk_w, chunk_wait[kStreamChunks], chunk_done[kStreamChunks];
     uint32_t *status;
 };
 int launch_decode(const DecodeArgs &a, cudaStream_t stream);
+
+// One (geometry, erasure mask) of a batch: its reconstruction path, as the
+// decode kernels read it from device memory.
+struct DecGroup {
+    const uint32_t *steps;          // T step words then T forward words (device)
+    int32_t T;
+    uint32_t fwd;                   // operand pattern of the steady steps
+    int32_t p[2 * kMaxLines];       // direction of front (l, side), index 2l + side
+    int32_t src[2 * kMaxLines];     // bin of pixel x of that front: word src - x
+    int32_t split[kMaxLines];       // x < split[l]: left front
+    int32_t chunk_w;                // streamed chunks (see Schedule)
+    int32_t chunk_wait[kStreamChunks];
+    int32_t chunk_done[kStreamChunks];
+};
+
+// One work item of a batched decode: nst (<= G) stripes of group `group`,
+// whose addresses sit at srcp/dstp[first .. first + nst).
+struct DecWork {
+    int32_t group;
+    int32_t nst;
+    int64_t first;
+};
+
+// Shared-memory layout of a decode launch (one warp per CTA).
+struct DecodeLayout {
+    int kernel;         // 0: decode_lines, 1: decode_fronts, 2: decode_stream
+    int reach, RP, SWc; // zero columns, row pitch, columns per stripe
+    int G, GS;          // stripes per work item, their interleave stride
+    int TS;             // words per step table (>= every group's steps, rounded)
+    int64_t smem;       // dynamic shared memory per CTA
+};
+int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, DecodeLayout *L);
+
+struct DecBatchArgs {
+    int P, Q;
+    int maxp, maxT;                 // over the groups (layout)
+    const DecGroup *groups;         // device
+    const DecWork *work;            // device
+    int64_t nwork;
+    const uint64_t *const *srcp;    // device: projection block of each stripe
+    uint64_t *const *dstp;          // device: image of each stripe
+    uint32_t *status;
+};
+int launch_decode_batched(const DecBatchArgs &a, const DecodeConfig &cfg, cudaStream_t stream);
 
 // Largest schedule (in steps) mojette_decode_noalloc accepts.
 constexpr int kNoAllocMaxSteps = 16384;

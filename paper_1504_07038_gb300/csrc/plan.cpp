@@ -118,6 +118,42 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
             for (size_t t = 0; t < steps.size(); ++t)
                 if (steps[t] == all && pattern[t] == fwd) steps[t] |= kStepSteady;
     }
+    // Streamed chunks: by distance from the end each front starts at.
+    {
+        int dmax = 1;
+        for (int l = 0; l < Q; ++l) dmax = std::max(dmax, std::max(a[l], P - a[l]));
+        const int cw = (dmax + kStreamChunks - 1) / kStreamChunks;
+        const int T = (int)steps.size();
+        int first[kStreamChunks], last[kStreamChunks];
+        for (int c = 0; c < kStreamChunks; ++c) {
+            first[c] = T;
+            last[c] = -1;
+        }
+        int cl[kMaxLines] = {}, cr[kMaxLines] = {};
+        for (int t = 0; t < T; ++t)
+            for (int l = 0; l < Q; ++l)
+                for (int side = 0; side < 2; ++side) {
+                    if (!(steps[t] >> (2 * l + side) & 1u)) continue;
+                    const int d = side ? cr[l]++ : cl[l]++;   // distance of the rebuilt pixel
+                    const int c = std::min(d / cw, kStreamChunks - 1);
+                    first[c] = std::min(first[c], t);
+                    last[c] = std::max(last[c], t);
+                }
+        out->chunk_w = cw;
+        // wait for chunk c before the first step that touches c or a later chunk
+        int m = T;
+        for (int c = kStreamChunks - 1; c >= 0; --c) {
+            m = std::min(m, first[c]);
+            out->chunk_wait[c] = m;
+        }
+        out->chunk_wait[0] = 0;
+        // chunk c is final once it and every earlier chunk are
+        int M = -1;
+        for (int c = 0; c < kStreamChunks; ++c) {
+            M = std::max(M, last[c]);
+            out->chunk_done[c] = M;
+        }
+    }
     out->fwd = fwd;
     out->T = (int)steps.size();
     out->steps = std::move(steps);

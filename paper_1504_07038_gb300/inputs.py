@@ -92,6 +92,20 @@ def erasure_counts(S: int, max_erasures: int, seed: int = DEFAULT_SEED,
     return (k % np.uint64(max_erasures + 1)).astype(np.int64)
 
 
+def categories(S: int, k: int, seed: int = DEFAULT_SEED, first: int = 0) -> np.ndarray:
+    """Per-stripe category in 0..k-1, uniform and seeded (e.g. which geometry
+    a stripe of a mixed batch uses)."""
+    s = np.arange(first, first + S, dtype=np.uint64)
+    c = splitmix64(seed ^ int(_MASK_STREAM) ^ 0xA5A5, s)
+    return (c % np.uint64(k)).astype(np.int64)
+
+
+def permutation(S: int, seed: int = DEFAULT_SEED) -> np.ndarray:
+    """A seeded permutation of 0..S-1 (stripes sorted by a counter-based key)."""
+    keys = splitmix64(seed ^ int(_MASK_STREAM) ^ 0x3C3C, np.arange(S, dtype=np.uint64))
+    return np.argsort(keys, kind="stable")
+
+
 def all_masks(n: int, erasures: int):
     """Every mask of n projections with exactly ``erasures`` bits set."""
     out = []
