@@ -199,7 +199,7 @@ typedef struct mojette_batch_s *mojette_batch_t;
  * for decode, by erasure mask -- one reconstruction path each (Sec. 2.2),
  * computed and cached in the plan as by mojette_decode. Builds the device
  * tables (per-stripe addresses, paths, work items: about 16 bytes per stripe
- * plus 336 bytes per (plan, mask)) and uploads them; blocking. The stripes
+ * plus about 380 bytes per (plan, mask)) and uploads them; blocking. The stripes
  * array is read, not retained. Buffers must not overlap between stripes
  * whose writes could collide.
  * Errors: -EINVAL (null plan or pointer, bad op, mask bits beyond n, decode
@@ -237,8 +237,9 @@ int mojette_batch_run(mojette_batch_t batch, mojette_stream_t stream);
  * the batch: for decode the kernel (decode_lines, one lane per line and
  * front; decode_stream, the same lanes with the stripe streamed through
  * shared memory in chunks; decode_fronts, one lane per front), stripes per
- * CTA, persistent or one-shot grids and the shared-memory row pitch; for
- * encode the stripes per shared-memory tile. Each
+ * CTA, persistent or one-shot grids and whether each line's row starts at
+ * the bank phase chosen for the path; for encode the stripes per
+ * shared-memory tile. Each
  * candidate runs 1 + reps times on `stream` (so the batch's outputs are
  * written, with their correct values) and is timed with CUDA events; the
  * fastest is kept in the batch and in the plan, where later batches of the
@@ -254,7 +255,7 @@ int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps)
  *   configs     6 words per launch: op, Q, P, then for decode the kernel
  *               (0 decode_lines, 1 decode_fronts, 2 decode_stream), work
  *               items per CTA and
- *               flags (bit 0 persistent grid, bit 1 bank-spread row pitch),
+ *               flags (bit 0 persistent grid, bit 1 bank-phased rows),
  *               for encode 0, the tile bytes (0 = default) and 0. The array
  *               holds 6 * launches words.
  */

@@ -34,6 +34,7 @@ struct Klass {
     int64_t wbase = 0, wcap = 0;    // its region of the work table
     int64_t nwork = 0;              // work items in use
     int maxp = 0, maxT = 0;
+    int32_t rowoff[kMaxLines] = {};   // row phases of its largest group
     DecodeConfig dcfg;
     EncodeConfig ecfg;
 };
@@ -104,7 +105,7 @@ int fill_work(Batch &b, Klass &k, int G)
 
 int class_layout(const Klass &k, const DecodeConfig &cfg, DecodeLayout *L)
 {
-    return decode_layout(k.plan->P, k.plan->Q, k.maxp, k.maxT, cfg, L);
+    return decode_layout(k.plan->P, k.plan->Q, k.maxp, k.maxT, cfg, k.rowoff, L);
 }
 
 int launch_class(Batch &b, const Klass &k, cudaStream_t st)
@@ -135,6 +136,7 @@ int launch_class(Batch &b, const Klass &k, cudaStream_t st)
     a.Q = k.plan->Q;
     a.maxp = k.maxp;
     a.maxT = k.maxT;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = k.rowoff[l];
     a.groups = group_table(b, b.dev);
     a.work = work_table(b, b.dev) + k.wbase;
     a.nwork = k.nwork;
@@ -253,6 +255,8 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         } else {
             k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : DecodeConfig();
             k.gbase = (int64_t)groups.size();
+            int64_t big = 0;
+            Schedule *big_sc = nullptr;
             for (int64_t g = r; g < e;) {
                 const uint32_t mask = stripes[idx[g]].erasure_mask;
                 int64_t h = g;
@@ -280,9 +284,17 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                     k.maxp = std::max(k.maxp, std::max(std::abs(sc->pL[l]), std::abs(sc->pR[l])));
                 }
                 k.maxT = std::max(k.maxT, sc->T);
+                if (h - g > big) {   // the largest group sets the class's row phases
+                    big = h - g;
+                    big_sc = sc;
+                }
                 groups.push_back(gr);
                 k.gcount.push_back(h - g);
                 g = h;
+            }
+            if (big_sc) {
+                const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
+                for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = ph[l];
             }
             // room for the smallest G any configuration uses (1 stripe per item)
             k.wcap = k.count;
@@ -434,7 +446,7 @@ int tune(Batch &b, cudaStream_t st, int reps)
             k.plan->enc_cfg = best_cfg;
             k.plan->tuned_enc = true;
         } else {
-            struct Cand { int kernel, gpc, persist, spread; };
+            struct Cand { int kernel, gpc, persist, rowoff; };
             std::vector<Cand> cands;
             if (k.plan->Q <= 8) {
                 for (int kern : {0, 2})
@@ -451,7 +463,7 @@ int tune(Batch &b, cudaStream_t st, int reps)
                 cfg.kernel = c.kernel;
                 cfg.gpc = c.gpc;
                 cfg.persist = c.persist;
-                cfg.spread = c.spread;
+                cfg.rowoff = c.rowoff;
                 DecodeLayout L;
                 if (class_layout(k, cfg, &L)) continue;      // does not fit: skip
                 if (c.kernel != L.kernel) continue;           // Q > 8: decode_fronts only
@@ -586,7 +598,7 @@ int mojette_batch_info(mojette_batch_t batch, int64_t *launches, int64_t *groups
             c[2] = k.plan->P;
             c[3] = k.op == MOJETTE_OP_DECODE ? k.dcfg.kernel : 0;
             c[4] = k.op == MOJETTE_OP_DECODE ? k.dcfg.gpc : k.ecfg.tile_bytes;
-            c[5] = k.op == MOJETTE_OP_DECODE ? (k.dcfg.persist | (k.dcfg.spread << 1)) : 0;
+            c[5] = k.op == MOJETTE_OP_DECODE ? (k.dcfg.persist | (k.dcfg.rowoff << 1)) : 0;
         }
     return 0;
 }

@@ -8,7 +8,14 @@
 
 namespace mojette {
 
-int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, DecodeLayout *L)
+int decode_bank_slots(int Q)
+{
+    const int G = std::max(1, 32 / (2 * Q));
+    return (16 % G == 0 && G < 16) ? 16 / G : 1;
+}
+
+int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, const int32_t *rowoff,
+                  DecodeLayout *L)
 {
     int err = 0, dev = 0, cap = 0, cap_sm = 0;
     if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
@@ -22,6 +29,7 @@ int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, Dec
     L->reach = (Q - 1) * maxp + 1;
     L->RP = P + L->reach;
     L->TS = (maxT + 3) / 4 * 4 + 4;
+    for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = L->reach + l * L->RP;
     const int want = (cfg.kernel == 1 || Q > 8) ? 1 : cfg.kernel;
     L->kernel = want;
     if (want == 2) {
@@ -31,28 +39,26 @@ int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, Dec
         L->GS = L->G;
         L->reach = 0;
         L->RP = P;
-        if (cfg.spread && 16 % L->G == 0 && L->G < 16) {
-            const int slots = 16 / L->G;
-            while (L->RP % slots != 1) ++L->RP;
-        }
+        for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = l * L->RP;
         L->SWc = Q * L->RP + 1;
         L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
         return L->smem > cap ? -EINVAL : 0;
     }
     if (want == 0) {
-        // decode_lines: 2Q lanes per stripe; step and forward words first
+        // decode_lines: 2Q lanes per stripe; step and forward words first.
+        // With row phases, line l's row starts at a column congruent to
+        // rowoff[l] mod S (the bank slots of a group of G words): the pitch
+        // gains S - 1 columns so that every gap between rows keeps at least
+        // `reach` zero columns.
         L->G = std::max(1, 32 / (2 * Q));
         L->GS = L->G;
-        // The lanes of one (line, front) read G consecutive words, a run
-        // that starts on one of 16 / G bank slots of a 128-byte wavefront
-        // (the column times G, mod 16). With a row pitch of 1 mod 16 / G,
-        // the lines of a front start on successive slots instead of
-        // sharing one. The extra columns join the zero columns before each
-        // row (reach = RP - P).
-        if (cfg.spread && 16 % L->G == 0 && L->G < 16) {
-            const int slots = 16 / L->G;
-            while (L->RP % slots != 1) ++L->RP;
-            L->reach = L->RP - P;
+        const int S = decode_bank_slots(Q);
+        if (cfg.rowoff && rowoff && S > 1) {
+            L->RP = P + L->reach + (S - 1);
+            for (int l = 0; l < Q; ++l) {
+                const int base = L->reach + l * L->RP;
+                L->rowbase[l] = base + (((rowoff[l] - base) % S) + S) % S;
+            }
         }
         L->SWc = Q * L->RP + L->reach;
         L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
@@ -123,9 +129,9 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         else if (strcmp(kenv, "stream") == 0) cfg.kernel = 2;
     }
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
-    if (const char *e = getenv("MOJETTE_DECODE_SPREAD")) cfg.spread = atoi(e) ? 1 : 0;
+    if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
     DecodeLayout L;
-    int err = decode_layout(d.P, d.Q, maxp, d.T, cfg, &L);
+    int err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
     if (err) return err;
     return launch_decode_kernel<false>(a, L, cfg, (d.S + L.G - 1) / L.G, st);
 }

@@ -8,7 +8,7 @@ namespace mojette {
 int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaStream_t st)
 {
     DecodeLayout L;
-    int err = decode_layout(b.P, b.Q, b.maxp, b.maxT, cfg, &L);
+    int err = decode_layout(b.P, b.Q, b.maxp, b.maxT, cfg, b.rowoff, &L);
     if (err) return err;
     DecParams a;
     std::memset(&a, 0, sizeof(a));

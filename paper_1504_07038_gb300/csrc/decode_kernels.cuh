@@ -59,7 +59,9 @@ struct DecParams {
     int64_t total;
     int P, Q;
     int reach;    // zero columns before, between and after the rows of a stripe
-    int RP;       // row pitch in columns: P + reach
+    int RP;       // row pitch in columns: P + reach (+ room for row phases)
+    int SWc;      // columns per stripe slot
+    int rowbase[kMaxLines];   // decode_lines: first column of each line's row
     int G;        // stripes per work item (one warp)
     int GS;       // interleave stride (decode_lines: G; decode_fronts: G rounded to odd)
     int TS;       // words per step table in shared memory
@@ -339,8 +341,10 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
     uint32_t *fwdw = stepw + a.TS;
     uint64_t *wbuf = sm + a.TS;
-    for (int ll = 0; ll <= Q; ++ll)
-        for (int i = lane; i < a.reach * G; i += 32) wbuf[ll * a.RP * G + i] = 0;
+    // Zero the stripe slots once: rows are always staged before they are
+    // read and the columns around them (pixels outside the image, the XOR
+    // identity) are never written.
+    for (int i = lane; i < a.SWc * G; i += 32) wbuf[i] = 0;
     const uint32_t wbase = smem_addr(wbuf);
 
     // Rebuild lanes: lane = (2l + side) * G + g; lanes past 2Q*G shadow lane 0.
@@ -350,7 +354,8 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     const int g = ok ? lane - lsr * G : 0;
     const int l = ls >> 1, side = ls & 1;
     const uint32_t bitmask = ok ? 1u << ls : 0u;   // shadow lanes never store
-    const uint32_t start = wbase + ((a.reach + l * a.RP + (side ? P - 1 : 0)) * G + g) * 8;
+    const int myrow = a.rowbase[l];
+    const uint32_t start = wbase + ((myrow + (side ? P - 1 : 0)) * G + g) * 8;
     const int stepb = (side ? -1 : 1) * G * 8;
     const uint32_t has_next = (l + 1 < Q) ? 1u : 0u;
 
@@ -372,14 +377,12 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             stepw[t] = t < T ? gr.steps[t] : 0u;
             fwdw[t] = t < T ? gr.steps[T + t] : 0u;
         }
+        // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
         const int p = gr.p[ls];
-        const int colstep = (a.RP + p) * G * 8;   // bytes from line l to line l+1 on a bin line
-        d0 = (has_next ? 1 : 1 - Q) * colstep;
+        auto off = [&](int l2) { return (a.rowbase[l2] - myrow + (l2 - l) * p) * G * 8; };
+        d0 = off(has_next ? l + 1 : 0);
 #pragma unroll
-        for (int k = 1; k < Q - 1; ++k) {
-            const int l2 = (l + 1 + k) % Q;
-            dk[k - 1] = (l2 - l) * colstep;
-        }
+        for (int k = 1; k < Q - 1; ++k) dk[k - 1] = off((l + 1 + k) % Q);
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
         uint32_t c[Q];
 #pragma unroll
@@ -402,7 +405,8 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     if constexpr (!BATCHED) load_group(a.grp);
     __syncwarp();
 
-    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes.
+    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes (the G
+    // stripes of a column on adjacent lanes: contiguous shared-memory words).
     const int XK = 32 / G;
     const int xk = lane / G, gg = lane - xk * G;
     const bool copy_ok = xk < XK;
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             for (int ll = 0; ll < Q; ++ll) {
                 const int sp = grp().split[ll];
                 const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
-                uint64_t *dst = wbuf + (a.reach + ll * a.RP) * G + gg;
+                uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
                 for (int x = xk; x < P; x += XK)
                     cp_async8(dst + x * G, src + ((x < sp ? sl : sr) - x));
             }
@@ -442,8 +446,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         __syncwarp();
 
         uint32_t pos = start;
+        // the next step's words are read one step ahead (the tables hold
+        // T4 + 4 words, so the read past the last step stays inside them)
+        uint32_t w_next = stepw[0], f_next = fwdw[0];
         for (int t = 0; t < T4; ++t) {
-            const uint32_t w = stepw[t];
+            const uint32_t w = w_next, f = f_next;
+            w_next = stepw[t + 1];
+            f_next = fwdw[t + 1];
             if (w & kStepSteady) {
                 // steady: every line moves, links are the path's pattern
                 uint64_t v = ld_s64(pos);
@@ -460,7 +469,6 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 __syncwarp();
                 continue;
             }
-            const uint32_t f = fwdw[t];
             const uint32_t act = w & bitmask;
             const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
             uint64_t v = ld_s64(pos);
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         if (copy_ok && gg < nst) {
             uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
             for (int ll = 0; ll < Q; ++ll) {
-                const uint64_t *buf = wbuf + (a.reach + ll * a.RP) * G + gg;
+                const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
                 for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * G]);
             }
         }
@@ -788,6 +796,8 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
 {
     a.reach = L.reach;
     a.RP = L.RP;
+    a.SWc = L.SWc;
+    for (int l = 0; l < kMaxLines; ++l) a.rowbase[l] = L.rowbase[l];
     a.G = L.G;
     a.GS = L.GS;
     a.TS = L.TS;

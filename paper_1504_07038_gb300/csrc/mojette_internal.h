@@ -57,6 +57,11 @@ struct Schedule {
     int32_t chunk_w = 1;
     int32_t chunk_wait[kStreamChunks] = {};
     int32_t chunk_done[kStreamChunks] = {};
+    // decode_lines: column offset of each line's row in shared memory (mod
+    // the bank slots of its stripe groups), chosen so that the lanes of a
+    // warp read different banks at the steps of this path (plan.cpp).
+    int32_t rowoff[kMaxLines] = {};
+    bool phases_done = false;
     std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
 };
 
@@ -66,8 +71,8 @@ struct DecodeConfig {
     int kernel = 0;    // 0: decode_lines (Q <= 8), 1: decode_fronts, 2: decode_stream (Q <= 8)
     int gpc = 4;       // work items (groups of G stripes) per CTA
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
-    int spread = 0;    // decode_lines: 1 to pad the row pitch so that the lines of
-                       // a warp fall on different shared-memory banks
+    int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
+                       // bank phase (Schedule::rowoff), 0 at a uniform pitch
 };
 
 // Launch configuration of the encode kernel.
@@ -94,6 +99,8 @@ struct Plan {
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);
 // Returns the cached schedule (building it on a miss) or sets *err.
 Schedule *get_schedule(Plan &pl, uint32_t mask, int *err);
+// decode_lines row phases of a schedule (computed on first use, cached).
+const int32_t *schedule_row_phases(Plan &pl, Schedule &sc);
 // Device copy of a schedule's step words on the current device.
 int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev);
 int record_cuda(cudaError_t e);     // remembers e; returns 0 or -EIO
@@ -129,6 +136,7 @@ struct DecodeArgs {
     int32_t pL[kMaxLines], pR[kMaxLines], split[kMaxLines];
     int64_t srcL[kMaxLines], srcR[kMaxLines];
     int32_t chunk_w, chunk_wait[kStreamChunks], chunk_done[kStreamChunks];
+    int32_t rowoff[kMaxLines];
     uint32_t *status;
 };
 int launch_decode(const DecodeArgs &a, cudaStream_t stream);
@@ -161,13 +169,19 @@ struct DecodeLayout {
     int reach, RP, SWc; // zero columns, row pitch, columns per stripe
     int G, GS;          // stripes per work item, their interleave stride
     int TS;             // words per step table (>= every group's steps, rounded)
+    int rowbase[kMaxLines];   // first column of each line's row
     int64_t smem;       // dynamic shared memory per CTA
 };
-int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, DecodeLayout *L);
+// rowoff: decode_lines row offsets (may be null: none).
+int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, const int32_t *rowoff,
+                  DecodeLayout *L);
+// Bank slots of one stripe group of decode_lines / decode_stream for Q lines.
+int decode_bank_slots(int Q);
 
 struct DecBatchArgs {
     int P, Q;
     int maxp, maxT;                 // over the groups (layout)
+    int32_t rowoff[kMaxLines];      // decode_lines row offsets for the launch
     const DecGroup *groups;         // device
     const DecWork *work;            // device
     int64_t nwork;

@@ -172,6 +172,117 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
     return out->T;
 }
 
+// Shared-memory bank phases of the lines for decode_lines (one lane per
+// (line, front, stripe); the G stripes of a lane group sit in G consecutive
+// 8-byte words, so a group fills one of S = 16 / G bank slots of a 128-byte
+// wavefront: slot = (row start + column) mod S). A warp's 64-bit load is
+// served per half-warp (lanes 0-15, 16-31; measured on GB300: the count of
+// load wavefronts follows this model, not a whole-warp one); within a half,
+// groups that read different words in the same slot serialise (a bank
+// conflict). The row phases e_l = (row start of line l) mod S are free: this
+// replays the path's loads -- the own bin and the other lines' pixels of
+// every front at every step, the forwarded operand excluded -- and picks the
+// phases that minimise the summed worst-slot occupancy of both halves (the
+// wavefronts), by coordinate descent from a few deterministic starts.
+void choose_row_phases(const Plan &pl, Schedule *sc)
+{
+    sc->phases_done = true;
+    const int P = pl.P, Q = pl.Q;
+    for (int l = 0; l < kMaxLines; ++l) sc->rowoff[l] = 0;
+    if (Q < 2 || Q > 8) return;
+    const int G = std::max(1, 32 / (2 * Q));
+    if (16 % G != 0 || G >= 16) return;
+    const int S = 16 / G;
+    const int T = sc->T;
+    // Every step is replayed to track the fronts; the cost counts at most
+    // 96 of them, evenly spaced.
+    const int stride = std::max(1, (T + 95) / 96);
+    const int TC = (T + stride - 1) / stride;
+    // loads[t / stride][k][front] = (line, column) or line -1: no access
+    struct Acc { int8_t line; int16_t col; };
+    const int K = Q;   // own + Q-1 operands
+    std::vector<Acc> acc((size_t)TC * K * 2 * Q);
+    int x[2][kMaxLines];
+    for (int l = 0; l < Q; ++l) { x[0][l] = 0; x[1][l] = P - 1; }
+    for (int t = 0; t < T; ++t) {
+        const uint32_t w = sc->steps[(size_t)t], f = sc->fwdw[(size_t)t];
+        for (int l = 0; l < Q; ++l)
+            for (int side = 0; side < 2; ++side) {
+                const int fr = 2 * l + side;
+                const int p = side ? sc->pR[l] : sc->pL[l];
+                const int xx = x[side][l];
+                if (t % stride) continue;
+                Acc *a = &acc[((size_t)(t / stride) * K) * 2 * Q];
+                a[0 * 2 * Q + fr] = {(int8_t)l, (int16_t)xx};
+                for (int k = 0; k < Q - 1; ++k) {
+                    const int l2 = (l + 1 + k) % Q;
+                    const bool fwd = (k == 0 && l + 1 < Q && ((f >> fr) & 1u));
+                    a[(1 + k) * 2 * Q + fr] = fwd ? Acc{-1, 0} : Acc{(int8_t)l2, (int16_t)(xx + (l2 - l) * p)};
+                }
+            }
+        for (int l = 0; l < Q; ++l)
+            for (int side = 0; side < 2; ++side)
+                if ((w >> (2 * l + side)) & 1u) x[side][l] += side ? -1 : 1;
+    }
+    auto cost = [&](const int *e) {
+        int64_t c = 0;
+        int cnt[2][16];
+        Acc seen[2][16][16];
+        for (size_t b = 0; b < (size_t)TC * K; ++b) {
+            const Acc *a = &acc[b * 2 * Q];
+            for (int h = 0; h < 2; ++h)
+                for (int q = 0; q < S; ++q) cnt[h][q] = 0;
+            int worst[2] = {0, 0};
+            for (int fr = 0; fr < 2 * Q; ++fr) {
+                if (a[fr].line < 0) continue;
+                const int h = (fr * G) / 16;   // half-warp of the group's lanes
+                const int q = ((e[a[fr].line] + a[fr].col) % S + S) % S;
+                bool dup = false;
+                for (int i = 0; i < cnt[h][q]; ++i)
+                    if (seen[h][q][i].line == a[fr].line && seen[h][q][i].col == a[fr].col) dup = true;
+                if (dup) continue;
+                seen[h][q][cnt[h][q]++] = a[fr];
+                worst[h] = std::max(worst[h], cnt[h][q]);
+            }
+            c += worst[0] + worst[1];
+        }
+        return c;
+    };
+    int best[kMaxLines] = {}, e[kMaxLines];
+    int64_t best_c = -1;
+    uint32_t rng = 0x9E3779B9u ^ (uint32_t)(P * 131 + Q) ^ sc->mask;
+    for (int start = 0; start < 3; ++start) {
+        for (int l = 0; l < Q; ++l) {
+            rng = rng * 1664525u + 1013904223u;
+            e[l] = start == 0 ? 0 : (int)(rng >> 16) % S;
+        }
+        int64_t c = cost(e);
+        for (bool improved = true; improved;) {
+            improved = false;
+            for (int l = 0; l < Q; ++l) {
+                const int keep = e[l];
+                for (int v = 0; v < S; ++v) {
+                    if (v == keep) continue;
+                    e[l] = v;
+                    const int64_t cv = cost(e);
+                    if (cv < c) {
+                        c = cv;
+                        improved = true;
+                    } else {
+                        e[l] = keep;
+                    }
+                    if (e[l] != keep) break;
+                }
+            }
+        }
+        if (best_c < 0 || c < best_c) {
+            best_c = c;
+            for (int l = 0; l < Q; ++l) best[l] = e[l];
+        }
+    }
+    for (int l = 0; l < Q; ++l) sc->rowoff[l] = best[l];
+}
+
 // Cap on the number of Q-subsets of the survivors tried per mask.
 constexpr int kMaxCandidates = 512;
 
@@ -276,6 +387,13 @@ int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev)
     sc.dev[device] = d;
     *dev = d;
     return 0;
+}
+
+const int32_t *schedule_row_phases(Plan &pl, Schedule &sc)
+{
+    std::lock_guard<std::mutex> g(pl.mu);
+    if (!sc.phases_done) choose_row_phases(pl, &sc);
+    return sc.rowoff;
 }
 
 }  // namespace mojette

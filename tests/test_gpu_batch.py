@@ -165,16 +165,15 @@ def test_every_tuner_candidate_is_exact(monkeypatch):
     proj = oracle.encode(img, p, threads=8)
     d_proj = torch.from_numpy(proj.view(np.int64)).cuda()
     mask = 0b000011000011
-    for kernel in ("lines", "fronts", "stream"):
-        for gpc in ("1", "3", "8"):
-            for spread in ("0", "1"):
-                monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
-                monkeypatch.setenv("MOJETTE_DECODE_GPC", gpc)
-                monkeypatch.setenv("MOJETTE_DECODE_SPREAD", spread)
-                out = torch.zeros((133, Q, P), dtype=torch.int64, device="cuda")
-                mj.mojette_decode(plan, d_proj, mask, out)
-                torch.cuda.synchronize()
-                assert np.array_equal(out.cpu().numpy().view(np.uint64), img), (kernel, gpc, spread)
+    cases = [(k, g, r) for k in ("lines", "fronts", "stream") for g in ("1", "3", "8") for r in ("0", "1")]
+    for kernel, gpc, rowoff in cases:
+        monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+        monkeypatch.setenv("MOJETTE_DECODE_GPC", gpc)
+        monkeypatch.setenv("MOJETTE_DECODE_ROWOFF", rowoff)
+        out = torch.zeros((133, Q, P), dtype=torch.int64, device="cuda")
+        mj.mojette_decode(plan, d_proj, mask, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), img), (kernel, gpc, rowoff)
 
 
 def test_batch_update_and_mixed_ops():
