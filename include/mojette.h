@@ -235,8 +235,9 @@ int mojette_batch_run(mojette_batch_t batch, mojette_stream_t stream);
 /*
  * mojette_batch_tune -- autotune the launch configuration of every class of
  * the batch: for decode the kernel (decode_lines, one lane per line and
- * front; decode_stream, the same lanes with the stripe streamed through
- * shared memory in chunks; decode_fronts, one lane per front), stripes per
+ * front; decode_cols, the same lanes over a line-interleaved layout;
+ * decode_stream, the same lanes with the stripe streamed through shared
+ * memory in chunks; decode_fronts, one lane per front), stripes per
  * CTA, persistent or one-shot grids and whether each line's row starts at
  * the bank phase chosen for the path; for encode the stripes per
  * shared-memory tile. Each
@@ -253,7 +254,8 @@ int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps)
  *   groups      (plan, mask) groups of the decode stripes;
  *   work_items  decode work items (one warp's stripes each);
  *   configs     6 words per launch: op, Q, P, then for decode the kernel
- *               (0 decode_lines, 1 decode_fronts, 2 decode_stream), work
+ *               (0 decode_lines, 1 decode_fronts, 2 decode_stream,
+ *               3 decode_cols), work
  *               items per CTA and
  *               flags (bit 0 persistent grid, bit 1 bank-phased rows),
  *               for encode 0, the tile bytes (0 = default) and 0. The array

@@ -292,7 +292,7 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 k.gcount.push_back(h - g);
                 g = h;
             }
-            if (big_sc) {
+            if (big_sc && k.count >= kPhaseMinStripes) {
                 const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
                 for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = ph[l];
             }
@@ -449,11 +449,11 @@ int tune(Batch &b, cudaStream_t st, int reps)
             struct Cand { int kernel, gpc, persist, rowoff; };
             std::vector<Cand> cands;
             if (k.plan->Q <= 8) {
-                for (int kern : {0, 2})
-                    for (int sp : {0, 1})
-                        for (int g : {1, 2, 4, 8}) cands.push_back({kern, g, 0, sp});
-                cands.push_back({0, 4, 1, 1});
-                cands.push_back({2, 4, 1, 1});
+                for (int sp : {0, 1})
+                    for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});
+                for (int kern : {2, 3})
+                    for (int g : {1, 2, 4, 8}) cands.push_back({kern, g, 0, 0});
+                for (int kern : {0, 3}) cands.push_back({kern, 4, 1, 1});
             }
             for (int g : {1, 2, 4}) cands.push_back({1, g, 0, 0});
             float best = 1e30f;

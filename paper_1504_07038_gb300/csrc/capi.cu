@@ -166,8 +166,8 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
         a.srcL[l] = sc->srcL[l];
         a.srcR[l] = sc->srcR[l];
     }
-    const int32_t *ph = schedule_row_phases(*pl, *sc);
-    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph[l];
+    const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
     a.chunk_w = sc->chunk_w;
     for (int c = 0; c < kStreamChunks; ++c) {
         a.chunk_wait[c] = sc->chunk_wait[c];
@@ -211,8 +211,8 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
         a.srcL[l] = sc->srcL[l];
         a.srcR[l] = sc->srcR[l];
     }
-    const int32_t *ph = schedule_row_phases(*pl, *sc);
-    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph[l];
+    const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
     a.chunk_w = sc->chunk_w;
     for (int c = 0; c < kStreamChunks; ++c) {
         a.chunk_wait[c] = sc->chunk_wait[c];

@@ -44,6 +44,16 @@ int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, con
         L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
         return L->smem > cap ? -EINVAL : 0;
     }
+    if (want == 3) {
+        // decode_cols: columns of Q lines x G stripes, reach zero columns at
+        // both ends of the rows; step and forward words first
+        L->G = std::max(1, 32 / (2 * Q));
+        L->GS = L->G;
+        L->RP = 0;
+        L->SWc = (P + 2 * L->reach) * Q;
+        L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
+        return L->smem > cap ? -EINVAL : 0;
+    }
     if (want == 0) {
         // decode_lines: 2Q lanes per stripe; step and forward words first.
         // With row phases, line l's row starts at a column congruent to
@@ -127,6 +137,7 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     if (const char *kenv = getenv("MOJETTE_DECODE_KERNEL")) {
         if (strcmp(kenv, "fronts") == 0) cfg.kernel = 1;
         else if (strcmp(kenv, "stream") == 0) cfg.kernel = 2;
+        else if (strcmp(kenv, "cols") == 0) cfg.kernel = 3;
     }
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;

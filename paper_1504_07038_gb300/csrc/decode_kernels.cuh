@@ -503,6 +503,175 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
 }
 
 // ---------------------------------------------------------------------------
+// decode_cols: decode_lines' arithmetic with the lines interleaved as well as
+// the stripes. Word (line l, column c, stripe g) of a warp's slot sits at
+// ((c + reach) * Q + l) * G + g: one column of all Q lines of the G stripes
+// fills Q * G = 16 consecutive words (128 bytes, one shared-memory wavefront
+// row), so the bank slot of a word is its line. The lanes are split by
+// front: lanes 0..15 run the left fronts of lines 0..Q-1 (G lanes each),
+// lanes 16..31 the right fronts. In every load of a step, the lanes of one
+// front read Q different lines (their own, or line l+1+k mod Q for operand
+// k), hence Q different bank slots, whatever their columns: a 64-bit load
+// (served per half-warp) takes one wavefront per half instead of the
+// several that colliding rows cost. Columns of zeros pad both ends of the
+// rows (pixels outside the image, the XOR identity).
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32) decode_cols(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    const int P = a.P, G = a.G;
+    const int CW = Q * G;            // words per column
+    const int lane = threadIdx.x & 31;
+    uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
+    uint32_t *fwdw = stepw + a.TS;
+    uint64_t *wbuf = sm + a.TS;
+    for (int i = lane; i < a.SWc * G; i += 32) wbuf[i] = 0;
+    const uint32_t wbase = smem_addr(wbuf);
+
+    // Rebuild lanes: lane = 16 * side + l * G + g; lanes past Q*G in a half
+    // shadow line 0 of their side (same loads, no stores).
+    const int side = lane >> 4;
+    const int r = lane & 15;
+    const bool ok = r < CW;
+    const int l = ok ? r / G : 0;
+    const int g = ok ? r - (r / G) * G : 0;
+    const int ls = 2 * l + side;
+    const uint32_t bitmask = ok ? 1u << ls : 0u;
+    const uint32_t start = wbase + (((a.reach + (side ? P - 1 : 0)) * Q + l) * G + g) * 8;
+    const int stepb = (side ? -1 : 1) * CW * 8;
+    const uint32_t has_next = (l + 1 < Q) ? 1u : 0u;
+
+    int T4 = 0, d0 = 0;
+    int dk[Q > 2 ? Q - 2 : 1];
+    uint32_t sfw = 0u;
+    uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    auto load_group = [&](const DecGroup &gr) {
+        const int T = gr.T;
+        T4 = (T + 3) & ~3;
+        for (int t = lane; t < T4; t += 32) {
+            stepw[t] = t < T ? gr.steps[t] : 0u;
+            fwdw[t] = t < T ? gr.steps[T + t] : 0u;
+        }
+        // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
+        const int p = gr.p[ls];
+        auto off = [&](int l2) { return ((l2 - l) * p * Q + (l2 - l)) * G * 8; };
+        d0 = off(has_next ? l + 1 : 0);
+#pragma unroll
+        for (int k = 1; k < Q - 1; ++k) dk[k - 1] = off((l + 1 + k) % Q);
+        sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
+        uint32_t c[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
+#pragma unroll
+        for (int rr = 0, d = 1; d < Q; ++rr, d <<= 1) {
+            slink[rr] = ok ? c[l] : 0u;
+            uint32_t nc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+        }
+    };
+    const DecGroup *gp = nullptr;
+    auto grp = [&]() -> const DecGroup & {
+        if constexpr (BATCHED) return *gp;
+        else return a.grp;
+    };
+    if constexpr (!BATCHED) load_group(a.grp);
+    __syncwarp();
+
+    // Copy lanes: lane = (xk * Q + ll) * G + gg covers XC columns per pass,
+    // so adjacent lanes touch adjacent shared-memory words.
+    const int XC = 32 / CW;
+    const int xk = lane / CW, rem = lane - xk * CW;
+    const int ll = rem / G, gg = rem - (rem / G) * G;
+    const bool copy_ok = xk < XC;
+
+    int cur = -1;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            nst = wk.nst;
+            first = wk.first;
+            if (wk.group != cur) {
+                cur = wk.group;
+                gp = a.groups + cur;
+                __syncwarp();
+                load_group(*gp);
+                __syncwarp();
+            }
+        } else {
+            s0 = item * G;
+            nst = (int)min64(G, a.S - s0);
+        }
+
+        if (copy_ok && gg < nst) {
+            const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+            const int sp = grp().split[ll];
+            const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
+            uint64_t *dst = wbuf + (a.reach * Q + ll) * G + gg;
+            for (int x = xk; x < P; x += XC)
+                cp_async8(dst + x * CW, src + ((x < sp ? sl : sr) - x));
+        }
+        cp_async_wait_all();
+        __syncwarp();
+
+        uint32_t pos = start;
+        uint32_t w_next = stepw[0], f_next = fwdw[0];
+        for (int t = 0; t < T4; ++t) {
+            const uint32_t w = w_next, f = f_next;
+            w_next = stepw[t + 1];
+            f_next = fwdw[t + 1];
+            if (w & kStepSteady) {
+                uint64_t v = ld_s64(pos);
+#pragma unroll
+                for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
+                if (Q > 1) v ^= ld_s64_if(pos + d0, (sfw & has_next) ^ 1u);
+#pragma unroll
+                for (int rr = 0, d = 1; d < Q; ++rr, d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
+                    if (slink[rr]) v ^= tv;
+                }
+                st_s64_if(pos, v, ok);
+                pos += stepb;
+                __syncwarp();
+                continue;
+            }
+            const uint32_t act = w & bitmask;
+            const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
+            uint64_t v = ld_s64(pos);
+#pragma unroll
+            for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
+            if (Q > 1) v ^= ld_s64_if(pos + d0, (fw & has_next) ^ 1u);
+            uint32_t c = fw;
+#pragma unroll
+            for (int d = 1; d < Q; d <<= 1) {
+                const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
+                const uint32_t tc = __shfl_down_sync(0xffffffffu, c, d * G);
+                if (c) {
+                    v ^= tv;
+                    c = tc;
+                }
+            }
+            st_s64_if(pos, v, act);
+            pos += act ? stepb : 0;
+            __syncwarp();
+        }
+
+        if (copy_ok && gg < nst) {
+            uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+            const uint64_t *buf = wbuf + (a.reach * Q + ll) * G + gg;
+            for (int x = xk; x < P; x += XC) __stcs(out + ll * P + x, buf[x * CW]);
+        }
+        __syncwarp();
+    });
+}
+
+// ---------------------------------------------------------------------------
 // decode_stream: decode_lines' lanes and steps, with the stripe streamed
 // through shared memory instead of staged and written whole:
 //   - rows are packed at pitch RP (no zero columns between them); an operand
@@ -773,6 +942,22 @@ DecKernel pick_lines(int Q)
 }
 
 template <bool BATCHED>
+DecKernel pick_cols(int Q)
+{
+    switch (Q) {
+    case 1: return decode_cols<1, BATCHED>;
+    case 2: return decode_cols<2, BATCHED>;
+    case 3: return decode_cols<3, BATCHED>;
+    case 4: return decode_cols<4, BATCHED>;
+    case 5: return decode_cols<5, BATCHED>;
+    case 6: return decode_cols<6, BATCHED>;
+    case 7: return decode_cols<7, BATCHED>;
+    case 8: return decode_cols<8, BATCHED>;
+    default: return nullptr;
+    }
+}
+
+template <bool BATCHED>
 DecKernel pick_stream(int Q)
 {
     switch (Q) {
@@ -808,6 +993,7 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     if (nitems <= 0) return 0;
     DecKernel fn = L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
+                 : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
                                  : pick_fronts<BATCHED>(a.Q);
     if (!fn) return -EINVAL;
     int err = 0;

@@ -68,7 +68,8 @@ struct Schedule {
 // Launch configuration of the decode kernels (chosen by the autotuner for a
 // batch, else the defaults here).
 struct DecodeConfig {
-    int kernel = 0;    // 0: decode_lines (Q <= 8), 1: decode_fronts, 2: decode_stream (Q <= 8)
+    int kernel = 0;    // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
+                       // (all but decode_fronts for Q <= 8 only)
     int gpc = 4;       // work items (groups of G stripes) per CTA
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
     int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
@@ -99,8 +100,11 @@ struct Plan {
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);
 // Returns the cached schedule (building it on a miss) or sets *err.
 Schedule *get_schedule(Plan &pl, uint32_t mask, int *err);
-// decode_lines row phases of a schedule (computed on first use, cached).
+// decode_lines row phases of a schedule (computed on first use, cached; the
+// search takes milliseconds, so launches of fewer than kPhaseMinStripes
+// stripes use uniform rows instead, rowoff all zero).
 const int32_t *schedule_row_phases(Plan &pl, Schedule &sc);
+constexpr int64_t kPhaseMinStripes = 4096;
 // Device copy of a schedule's step words on the current device.
 int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev);
 int record_cuda(cudaError_t e);     // remembers e; returns 0 or -EIO
@@ -165,7 +169,7 @@ struct DecWork {
 
 // Shared-memory layout of a decode launch (one warp per CTA).
 struct DecodeLayout {
-    int kernel;         // 0: decode_lines, 1: decode_fronts, 2: decode_stream
+    int kernel;         // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
     int reach, RP, SWc; // zero columns, row pitch, columns per stripe
     int G, GS;          // stripes per work item, their interleave stride
     int TS;             // words per step table (>= every group's steps, rounded)

@@ -195,8 +195,8 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
     const int S = 16 / G;
     const int T = sc->T;
     // Every step is replayed to track the fronts; the cost counts at most
-    // 96 of them, evenly spaced.
-    const int stride = std::max(1, (T + 95) / 96);
+    // 32 of them, evenly spaced.
+    const int stride = std::max(1, (T + 31) / 32);
     const int TC = (T + stride - 1) / stride;
     // loads[t / stride][k][front] = (line, column) or line -1: no access
     struct Acc { int8_t line; int16_t col; };
@@ -251,7 +251,7 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
     int best[kMaxLines] = {}, e[kMaxLines];
     int64_t best_c = -1;
     uint32_t rng = 0x9E3779B9u ^ (uint32_t)(P * 131 + Q) ^ sc->mask;
-    for (int start = 0; start < 3; ++start) {
+    for (int start = 0; start < 2; ++start) {
         for (int l = 0; l < Q; ++l) {
             rng = rng * 1664525u + 1013904223u;
             e[l] = start == 0 ? 0 : (int)(rng >> 16) % S;
