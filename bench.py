@@ -71,7 +71,8 @@ BATCHED = dict(S=500000,
                                  "p=+-1..3, (12,8) p=+-1..6, 0..n-k seeded erasures each, random order; "
                                  "one step = encode every stripe, then decode every stripe")
 METRIC = "Mojette encode/decode user-data GB/s & % HBM roofline; batched vs plain, 1 GB300"
-KERNEL_SOURCES = ["encode.cu", "decode.cu", "ptx.cuh", "mojette_internal.h"]
+KERNEL_SOURCES = ["encode_kernels.cuh", "decode_kernels.cuh", "encode.cu", "decode.cu", "ptx.cuh",
+                  "mojette_internal.h"]
 
 
 def decode_kernel_name(Q: int) -> str:

@@ -141,6 +141,7 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     }
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
+    if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;
     DecodeLayout L;
     int err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
     if (err) return err;
