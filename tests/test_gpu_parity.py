@@ -209,7 +209,8 @@ def test_full_size_wide_geometry():
     _full_size(128, 8, TWELVE, 262144, ms[7::83])
 
 
-VARIANTS = [("lines", None), ("fronts", None)]
+VARIANTS = [("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts", {}), ("stream", {}),
+            ("cols", {})]
 
 
 @pytest.mark.parametrize("kernel,K", VARIANTS)
@@ -217,9 +218,12 @@ VARIANTS = [("lines", None), ("fronts", None)]
                          + [("tiny(6,3)", 20, 3, [-4, -1, 0, 2, 5, 6]),
                             ("odd P(8,6)", 33, 6, [-4, -3, -1, 1, 2, 3, 5, 7])])
 def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
-    """Each decode kernel (decode_lines, decode_fronts), every k-of-n mask
-    (sampled at (12,8)), bit-exact."""
+    """Each decode kernel (decode_lines with and without row phases,
+    decode_fronts, decode_stream, decode_cols), every k-of-n mask (sampled
+    at (12,8)), bit-exact."""
     monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+    for k, v in K.items():
+        monkeypatch.setenv(k, v)
     S = 53
     n = len(p)
     img = inputs.stripes(S, Q, P, seed=P + Q)
