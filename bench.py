@@ -220,7 +220,7 @@ def run_gpu(args, w):
     plan = mj.mojette_plan(P, Q, p)
     stream = torch.cuda.current_stream()
 
-    img_np = inputs.stripes(S, Q, P, first=replica_first_stripe(rank, S))
+    img_np = inputs.stripes(S, Q, P, seed=args.seed, first=replica_first_stripe(rank, S))
     h_img = torch.from_numpy(img_np.view(np.int64)).pin_memory()
     del img_np
     d_img = h_img.cuda()
@@ -274,6 +274,10 @@ def run_gpu(args, w):
     barrier()
     enc_ms = [e[0][0].elapsed_time(e[0][1]) for e in events]
     dec_ms = [a.elapsed_time(b) for e in events for a, b in e[1:]]
+    # decode time per erasure mask (median over steps): the paper finds the
+    # cost independent of which projections are lost (Sec. 4, Fig. 2-3)
+    by_mask = [statistics.median(e[1 + k][0].elapsed_time(e[1 + k][1]) for e in events)
+               for k in range(len(masks))]
     total_ms = t0.elapsed_time(t1)
     clk = clocks.stop()
     total_ms = max_over_ranks(total_ms, dist)
@@ -298,6 +302,8 @@ def run_gpu(args, w):
     peak, peak_kind = measured_peaks()
     dec_gbs = dec_bytes / (dec_ms_avg * 1e-3) / 1e9
     dec_name = decode_kernel_name(Q)
+    # the ncu record was taken at the workload's own stripe count
+    traffic_key = args.workload if not args.stripes else None
     enc_gbs = enc_bytes / (enc_ms_avg * 1e-3) / 1e9
     line = {
         "metric": METRIC,
@@ -319,19 +325,22 @@ def run_gpu(args, w):
         "roofline": {"bound": "hbm", "kernel": dec_name, "achieved": round(dec_gbs, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
-                     "traffic": ncu_traffic(dec_name, args.workload),
+                     "traffic": ncu_traffic(dec_name, traffic_key),
                      "algorithmic_bytes_per_launch": dec_bytes},
         "kernels": {
             "encode_tiles": {"ms": round(enc_ms_avg, 4), "hbm_gbs": round(enc_gbs, 1),
                              "frac": round(enc_gbs / peak, 4),
                              "user_gbs": round(user_bytes / (enc_ms_avg * 1e-3) / 1e9, 1),
                              "algorithmic_bytes_per_launch": enc_bytes,
-                             "traffic": ncu_traffic("encode_tiles", args.workload)},
+                             "traffic": ncu_traffic("encode_tiles", traffic_key)},
             dec_name: {"ms": round(dec_ms_avg, 4), "hbm_gbs": round(dec_gbs, 1),
                        "frac": round(dec_gbs / peak, 4),
                        "user_gbs": round(user_bytes / (dec_ms_avg * 1e-3) / 1e9, 1),
                        "algorithmic_bytes_per_launch": dec_bytes,
-                       "traffic": ncu_traffic(dec_name, args.workload)},
+                       "traffic": ncu_traffic(dec_name, traffic_key),
+                       "ms_by_mask": {"min": round(min(by_mask), 4), "max": round(max(by_mask), 4),
+                                      "max_over_min": round(max(by_mask) / min(by_mask), 4),
+                                      "masks": len(masks)}},
         },
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
@@ -591,7 +600,7 @@ def run_reference(args, w):
     for _ in range(args.warmup):
         cpu_baseline(w, masks, budget_s=per_step)
     vals = [cpu_baseline(w, masks, budget_s=per_step) for _ in range(args.steps)]
-    v = statistics.median(x["value"] for x in vals)
+    v = round(statistics.median(x["value"] for x in vals), 4)
     cb = dict(vals[-1])
     cb["value"] = v
     user_step = w["S"] * w["Q"] * w["P"] * 8 * (1 + len(masks))
@@ -617,10 +626,15 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--seed", type=int, default=inputs.DEFAULT_SEED, help="seed of the stripe pixels")
+    ap.add_argument("--stripes", type=int, default=0, help="override the workload's stripe count")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.stripes:
+        w["S"] = args.stripes
+        w["desc"] = w["desc"] + f" (stripes set to {args.stripes})"
     line = run_reference(args, w) if args.impl == "reference" else run_gpu(args, w)
     if line is not None:
         print(json.dumps(line), flush=True)

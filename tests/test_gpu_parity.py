@@ -238,3 +238,30 @@ def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
         out.fill_(0x77)
         mj.mojette_decode(plan, d_proj, m, out, S)
         assert (host(out) == img).all(), (kernel, K, name, m)
+
+
+def test_decode_time_flat_across_masks():
+    """Sec. 4 (Fig. 2-3): decode cost does not depend on which projections
+    are lost. Every two-erasure mask of 8 KB (6,4) on 65536 stripes, timed
+    with CUDA events (median of 3): the slowest mask within 1.3x of the
+    fastest (the paths differ by at most a few steps)."""
+    P, Q, p, S = 256, 4, [-3, -2, -1, 1, 2, 3], 65536
+    plan = mj.mojette_plan(P, Q, p)
+    img = torch.from_numpy(inputs.stripes(S, Q, P, seed=3).view(np.int64)).cuda()
+    proj = torch.empty((S, plan.total), dtype=torch.int64, device="cuda")
+    out = torch.empty_like(img)
+    mj.mojette_encode(plan, img, proj, S)
+    times = []
+    for m in inputs.all_masks(len(p), 2):
+        mj.mojette_decode(plan, proj, m, out, S)          # warm-up, path cached
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mj.mojette_decode(plan, proj, m, out, S)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        times.append(sorted(ts)[1])
+        assert torch.equal(out, img), bin(m)
+    assert max(times) / min(times) < 1.3, times
