@@ -70,6 +70,36 @@ typedef struct mojette_plan_s *mojette_plan_t;
  */
 int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out);
 
+/* mojette_plan_ex flag: unused-bin removal. */
+#define MOJETTE_PLAN_TRIM_UNUSED 1u
+
+/*
+ * mojette_plan_ex -- mojette_plan with options (flags 0: the same plan).
+ * MOJETTE_PLAN_TRIM_UNUSED: store in each projection only the bins some
+ * reconstruction path of this library reads, over every erasure mask that
+ * leaves at least Q projections (Sec. 2.3 notes that some bins need not be
+ * stored and gives no rule; the rule here is that one). A trimmed
+ * projection holds those bins in increasing order (mojette_plan_bins gives
+ * each stored word's bin in the full projection of Eq. 2);
+ * mojette_plan_info reports the trimmed B_i, offsets and total. Encode
+ * writes exactly the stored bins; decode reads only them, for every mask
+ * with at least Q survivors. Building the plan builds the reconstruction
+ * path of every such mask (host only; a fraction of a second at n = 12);
+ * it requires n <= 20.
+ * Errors: as mojette_plan, -EINVAL for unknown flags or n > 20.
+ */
+int mojette_plan_ex(int P, int Q, const int *p, int n, uint32_t flags,
+                    mojette_plan_t *out);
+
+/*
+ * mojette_plan_bins -- for each stored word of a stripe's projection block
+ * (full_bin[total], may be NULL), the index of its bin in its projection's
+ * full layout (Eq. 2: j = b - b_min); the identity j = word - off_i for a
+ * plan that is not trimmed. Returns 1 for a trimmed plan, 0 for a full one,
+ * -EINVAL for NULL.
+ */
+int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin);
+
 /* Release a plan and every host and device resource it holds. Must not be
  * called while work that uses the plan is still in flight. NULL is a no-op. */
 int mojette_plan_destroy(mojette_plan_t plan);

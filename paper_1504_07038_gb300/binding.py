@@ -48,6 +48,8 @@ def lib():
             L = ctypes.CDLL(path)
             L.mojette_plan.argtypes = [_INT, _INT, _PTR, _INT, ctypes.POINTER(_PTR)]
             L.mojette_plan_destroy.argtypes = [_PTR]
+            L.mojette_plan_ex.argtypes = [_INT, _INT, _PTR, _INT, _U32, ctypes.POINTER(_PTR)]
+            L.mojette_plan_bins.argtypes = [_PTR, _PTR]
             L.mojette_plan_info.argtypes = [_PTR, _PTR, _PTR, _PTR]
             L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
@@ -69,7 +71,8 @@ def lib():
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
             L.mojette_last_cuda_error.argtypes = []
-            for name in ("mojette_plan", "mojette_plan_destroy", "mojette_plan_info",
+            for name in ("mojette_plan", "mojette_plan_ex", "mojette_plan_bins", "mojette_plan_destroy",
+                         "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc",
                          "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
                          "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
@@ -125,17 +128,28 @@ def _stream(stream) -> int:
     return stream.cuda_stream
 
 
-class Plan:
-    """Owns a ``mojette_plan_t``; geometry (P, Q, p) and its bin layout."""
+MOJETTE_PLAN_TRIM_UNUSED = 1
 
-    def __init__(self, P: int, Q: int, p):
+
+class Plan:
+    """Owns a ``mojette_plan_t``; geometry (P, Q, p) and its bin layout.
+    ``trim=True``: unused-bin removal (mojette_plan_ex); ``full_bin`` then
+    maps each stored word of a stripe's block to its bin in the full
+    projection (mojette_plan_bins)."""
+
+    def __init__(self, P: int, Q: int, p, trim: bool = False):
         self.P, self.Q, self.p = int(P), int(Q), [int(v) for v in p]
         arr = (ctypes.c_int * len(self.p))(*self.p)
         h = _PTR()
-        _check(lib().mojette_plan(self.P, self.Q, arr, len(self.p), ctypes.byref(h)), "mojette_plan")
+        flags = MOJETTE_PLAN_TRIM_UNUSED if trim else 0
+        _check(lib().mojette_plan_ex(self.P, self.Q, arr, len(self.p), flags, ctypes.byref(h)),
+               "mojette_plan_ex")
         self.handle = h.value
         self._lib = lib()
         self.bins, self.offsets, self.total = mojette_plan_info(self)
+        fb = np.zeros(max(1, self.total), dtype=np.int32)
+        self.trimmed = lib().mojette_plan_bins(self.handle, fb.ctypes.data) == 1
+        self.full_bin = fb[: self.total]
 
     @property
     def n(self) -> int:
@@ -155,6 +169,10 @@ class Plan:
 
 def mojette_plan(P: int, Q: int, p) -> Plan:
     return Plan(P, Q, p)
+
+
+def mojette_plan_ex(P: int, Q: int, p, flags: int = 0) -> Plan:
+    return Plan(P, Q, p, trim=bool(flags & MOJETTE_PLAN_TRIM_UNUSED))
 
 
 def mojette_plan_destroy(plan: Plan) -> None:

@@ -129,6 +129,7 @@ int launch_class(Batch &b, const Klass &k, cudaStream_t st)
         int err = 0;
         a.status = device_status_ptr(&err);
         if (err) return err;
+        if ((err = plan_full_bin_on_device(*k.plan, &a.full_bin))) return err;
         return launch_encode_batched(a, st);
     }
     DecBatchArgs a{};

@@ -1,4 +1,5 @@
 // extern "C" entry points of libmojette (declared in include/mojette.h).
+#include <algorithm>
 #include <cerrno>
 #include <cstring>
 #include <new>
@@ -80,6 +81,38 @@ int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out)
     return 0;
 }
 
+int mojette_plan_ex(int P, int Q, const int *p, int n, uint32_t flags, mojette_plan_t *out)
+{
+    if (!out) return -EINVAL;
+    *out = nullptr;
+    if (flags & ~(uint32_t)MOJETTE_PLAN_TRIM_UNUSED) return -EINVAL;
+    int err = mojette_plan(P, Q, p, n, out);
+    if (err) return err;
+    if (flags & MOJETTE_PLAN_TRIM_UNUSED) {
+        if ((err = trim_unused_bins(*reinterpret_cast<Plan *>(*out)))) {
+            mojette_plan_destroy(*out);
+            *out = nullptr;
+            return err;
+        }
+    }
+    return 0;
+}
+
+int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin)
+{
+    if (!plan) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (full_bin) {
+        if (pl->trimmed) {
+            std::copy(pl->full_bin.begin(), pl->full_bin.end(), full_bin);
+        } else {
+            for (int i = 0; i < pl->n; ++i)
+                for (int64_t j = 0; j < pl->B[i]; ++j) full_bin[pl->off[i] + j] = (int32_t)j;
+        }
+    }
+    return pl->trimmed ? 1 : 0;
+}
+
 int mojette_plan_destroy(mojette_plan_t plan)
 {
     if (!plan) return 0;
@@ -90,6 +123,8 @@ int mojette_plan_destroy(mojette_plan_t plan)
         for (auto &d : kv.second->dev) {
             if (have_device && cudaSetDevice(d.first) == cudaSuccess) cudaFree(d.second);
         }
+    for (auto &d : pl->full_bin_dev)
+        if (have_device && cudaSetDevice(d.first) == cudaSuccess) cudaFree(d.second);
     if (have_device) cudaSetDevice(cur);
     delete pl;
     return 0;
@@ -131,6 +166,7 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
     }
     a.status = device_status_ptr(&err);
     if (err) return err;
+    if ((err = plan_full_bin_on_device(*pl, &a.full_bin))) return err;
     return launch_encode(a, (cudaStream_t)stream);
 }
 

@@ -37,6 +37,7 @@ constexpr int kEncTileBytesNarrow = 9000;
 constexpr int kEncTileBytesWide = 24000;
 
 struct EncParams {
+    const int32_t *full_bin;        // trimmed plan: full bin index of each stored word, else null
     const uint64_t *img;            // plain: stripe s at img + s * Q * P
     uint64_t *proj;                 // plain: its bins at proj + s * total
     const uint64_t *const *srcp;    // batched: stripe s at srcp[s]
@@ -119,7 +120,8 @@ encode_tiles(const __grid_constant__ EncParams a)
         int i = 0;
         for (int q = 1; q < a.n; ++q)
             if (a.off[q] <= t) i = q;
-        const int c = -(t - a.off[i]) - a.bmin[i];
+        const int j = a.full_bin ? (t < a.total ? a.full_bin[t] : 0) : t - a.off[i];
+        const int c = -j - a.bmin[i];
         a0[k] = (uint32_t)((a.pad + c) * 8);
         stepc[k] = (RP + a.p[i]) * 8;
     }
@@ -225,7 +227,8 @@ __global__ void __launch_bounds__(256) encode_direct(const __grid_constant__ Enc
         int i = 0;
         for (int q = 1; q < a.n; ++q)
             if (a.off[q] <= t) i = q;
-        const int c = -(t - a.off[i]) - a.bmin[i];
+        const int j = a.full_bin ? a.full_bin[t] : t - a.off[i];
+        const int c = -j - a.bmin[i];
         const uint64_t *img = stripe_in<BATCHED>(a, s);
         uint64_t acc = 0;
         for (int l = 0; l < a.Q; ++l) {
@@ -284,6 +287,7 @@ template <bool BATCHED>
 int launch_encode_impl(const EncodeArgs &e, cudaStream_t st)
 {
     EncParams a;
+    a.full_bin = e.full_bin;
     a.img = e.img;
     a.proj = e.proj;
     a.srcp = e.srcp;

@@ -86,8 +86,17 @@ struct Plan {
     int32_t p[kMaxProj] = {};
     int64_t B[kMaxProj] = {};
     int64_t off[kMaxProj] = {};
-    int64_t bmin[kMaxProj] = {};
-    int64_t total = 0;
+    int64_t bmin[kMaxProj] = {};   // Eq. 2's b_min: bin j of the full projection is b = j + b_min
+    int64_t total = 0;             // stored words per stripe
+    // Unused-bin removal: a trimmed plan stores, for projection i, only the
+    // bins some reconstruction path reads, in order: stored word off_i + s
+    // holds full bin full_bin[off_i + s]; stored_of[fulloff_i + j] is the
+    // stored index s of full bin j (-1: not stored). Untrimmed: identity.
+    bool trimmed = false;
+    std::vector<int32_t> full_bin;     // total entries
+    std::vector<int32_t> stored_of;    // sum of the full B_i entries
+    int64_t fulloff[kMaxProj] = {};
+    std::map<int, int32_t *> full_bin_dev;   // device copy of full_bin, per device
     std::mutex mu;
     std::map<uint32_t, std::unique_ptr<Schedule>> schedules;
     // autotuned configurations (batch.cpp); used by batches of this plan
@@ -100,6 +109,12 @@ struct Plan {
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);
 // Returns the cached schedule (building it on a miss) or sets *err.
 Schedule *get_schedule(Plan &pl, uint32_t mask, int *err);
+// Unused-bin removal: keep in each projection only the bins some
+// reconstruction path reads, over every recoverable erasure mask.
+int trim_unused_bins(Plan &pl);
+// Device copy of a trimmed plan's stored-word -> full-bin map (null, 0 for a
+// plan that is not trimmed).
+int plan_full_bin_on_device(Plan &pl, const int32_t **dev);
 // decode_lines row phases of a schedule (computed on first use, cached; the
 // search takes milliseconds, so launches of fewer than kPhaseMinStripes
 // stripes use uniform rows instead, rowoff all zero).
@@ -112,6 +127,7 @@ uint32_t *device_status_ptr(int *err);  // per-device status word
 
 // ---- kernel launchers -------------------------------------------------------
 struct EncodeArgs {
+    const int32_t *full_bin;        // trimmed plan: full bin of each stored word (device), else null
     const uint64_t *img;            // plain: stripe s at img + s * Q * P
     uint64_t *proj;                 // plain: stripe s at proj + s * total
     const uint64_t *const *srcp;    // batched: stripe s at srcp[s] (device array)

@@ -22,6 +22,7 @@
 // replays it for every stripe that lost the same projections. Building it is
 // the paper's excluded pre-computation (Sec. 3.1).
 #include <algorithm>
+#include <cstdint>
 #include <cerrno>
 #include <cstring>
 #include <map>
@@ -166,8 +167,21 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
         out->pR[l] = pl.p[iR];
         out->split[l] = a[l];
         // bin j = l p - x - b_min at word off + j of the stripe block
-        out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
-        out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
+        // bin j = l p - x - b_min of the projection holds pixel x; the
+        // kernels read stored word src - x, so src is the stored word of the
+        // front's first pixel plus that pixel's x (a front reads one run of
+        // consecutive bins, all stored, hence consecutive stored words)
+        if (!pl.trimmed) {
+            out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
+            out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
+        } else {
+            const int sp = a[l];
+            auto stored = [&](int i, int64_t j) {
+                return (int64_t)pl.stored_of[(size_t)(pl.fulloff[i] + j)];
+            };
+            out->srcL[l] = sp > 0 ? pl.off[iL] + stored(iL, (int64_t)l * pl.p[iL] - pl.bmin[iL]) : 0;
+            out->srcR[l] = sp < P ? pl.off[iR] + stored(iR, (int64_t)l * pl.p[iR] - sp - pl.bmin[iR]) + sp : 0;
+        }
     }
     return out->T;
 }
@@ -394,6 +408,94 @@ const int32_t *schedule_row_phases(Plan &pl, Schedule &sc)
     std::lock_guard<std::mutex> g(pl.mu);
     if (!sc.phases_done) choose_row_phases(pl, &sc);
     return sc.rowoff;
+}
+
+// Unused-bin removal (Sec. 2.3 mentions that some bins need not be stored;
+// the paper gives no rule). Here a bin is unused when no reconstruction path
+// of this library reads it for any erasure mask that leaves at least Q
+// projections: the decoder reads bin l p - x - b_min of the projection
+// dedicated to line l for every pixel x of that line's front, one run of
+// consecutive bins per (line, front). A trimmed projection stores the bins
+// some path reads, in order; a run a path reads is then a run of
+// consecutive stored words too, so the decoder is unchanged but for its
+// base offsets, and the encoder computes each stored word from its full bin
+// index (Plan::full_bin). The paths are the cached ones, built here for
+// every mask; their offsets are rebuilt after the trim.
+int trim_unused_bins(Plan &pl)
+{
+    const int n = pl.n, Q = pl.Q, P = pl.P;
+    if (Q > kMaxLines || n > 20) return -EINVAL;
+    int64_t full = 0;
+    for (int i = 0; i < n; ++i) {
+        pl.fulloff[i] = full;
+        full += pl.B[i];
+    }
+    std::vector<uint8_t> used((size_t)full, 0);
+    int err = 0;
+    for (uint32_t mask = 0; mask < (1u << n); ++mask) {
+        if (__builtin_popcount(mask) > n - Q) continue;
+        Schedule *sc = get_schedule(pl, mask, &err);
+        if (!sc) return err;
+        for (int l = 0; l < Q; ++l) {
+            const int sp = sc->split[l];
+            for (int side = 0; side < 2; ++side) {
+                const int i = side ? sc->projR[l] : sc->projL[l];
+                const int x0 = side ? sp : 0, x1 = side ? P : sp;
+                for (int x = x0; x < x1; ++x)
+                    used[(size_t)(pl.fulloff[i] + (int64_t)l * pl.p[i] - x - pl.bmin[i])] = 1;
+            }
+        }
+    }
+    pl.stored_of.assign((size_t)full, -1);
+    pl.full_bin.clear();
+    int64_t t = 0;
+    for (int i = 0; i < n; ++i) {
+        pl.off[i] = t;
+        int32_t s = 0;
+        for (int64_t j = 0; j < pl.B[i]; ++j)
+            if (used[(size_t)(pl.fulloff[i] + j)]) {
+                pl.stored_of[(size_t)(pl.fulloff[i] + j)] = s++;
+                pl.full_bin.push_back((int32_t)j);
+            }
+        pl.B[i] = s;
+        t += s;
+    }
+    pl.total = t;
+    pl.trimmed = true;
+    std::lock_guard<std::mutex> g(pl.mu);
+    pl.schedules.clear();        // their bin offsets follow the full layout
+    return 0;
+}
+
+int plan_full_bin_on_device(Plan &pl, const int32_t **dev)
+{
+    *dev = nullptr;
+    if (!pl.trimmed) return 0;
+    int device = 0;
+    int r = record_cuda(cudaGetDevice(&device));
+    if (r) return r;
+    std::lock_guard<std::mutex> g(pl.mu);
+    auto it = pl.full_bin_dev.find(device);
+    if (it != pl.full_bin_dev.end()) {
+        *dev = it->second;
+        return 0;
+    }
+    int32_t *d = nullptr;
+    const size_t bytes = std::max<size_t>(4, pl.full_bin.size() * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        record_cuda(e);
+        return -ENOMEM;
+    }
+    if ((r = record_cuda(e))) return r;
+    if ((r = record_cuda(cudaMemcpy(d, pl.full_bin.data(), pl.full_bin.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice)))) {
+        cudaFree(d);
+        return r;
+    }
+    pl.full_bin_dev[device] = d;
+    *dev = d;
+    return 0;
 }
 
 }  // namespace mojette

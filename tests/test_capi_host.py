@@ -165,3 +165,38 @@ def test_schedule_for_every_small_geometry():
                         continue
                     sched = mj.mojette_schedule(plan, m)
                     assert (replay(sched, plan, proj, P, Q, p) == img).all(), (P, Q, p, m)
+
+
+TRIM_GEOMS = [(256, 4, [-3, -2, -1, 1, 2, 3]), (64, 8, [v for v in range(-6, 7) if v]),
+              (20, 3, [-4, -1, 0, 2, 5, 6])]
+
+
+@pytest.mark.parametrize("P,Q,p", TRIM_GEOMS)
+def test_trimmed_plan_keeps_every_bin_a_path_reads(P, Q, p):
+    """Unused-bin removal (Sec. 2.3): the stored bins of each projection are
+    in increasing order, and for every recoverable mask every run of bins a
+    front reads (bin l p - x - b_min, x over the front's pixels) is stored,
+    at consecutive stored words -- what the decoder's base offsets assume."""
+    from paper_1504_07038_gb300 import binding as mj
+    full = mj.mojette_plan(P, Q, p)
+    tr = mj.mojette_plan_ex(P, Q, p, mj.MOJETTE_PLAN_TRIM_UNUSED)
+    assert tr.trimmed and not full.trimmed
+    assert tr.total <= full.total and sum(tr.bins) == tr.total
+    assert list(full.full_bin) == [j for i in range(len(p)) for j in range(full.bins[i])]
+    where = {}
+    for i in range(len(p)):
+        fb = tr.full_bin[tr.offsets[i]: tr.offsets[i] + tr.bins[i]]
+        assert all(0 <= j < full.bins[i] for j in fb)
+        assert all(a < b for a, b in zip(fb, fb[1:]))
+        where[i] = {int(j): s for s, j in enumerate(fb)}
+    n = len(p)
+    for e in range(0, n - Q + 1):
+        for m in inputs.all_masks(n, e):
+            sc = mj.mojette_schedule(tr, m)
+            for l in range(Q):
+                for side, i in ((0, sc["left"][l]), (1, sc["right"][l])):
+                    xs = range(0, sc["split"][l]) if side == 0 else range(sc["split"][l], P)
+                    bmin = oracle.bin_min(p[i], P, Q)
+                    idx = [where[i].get(l * p[i] - x - bmin) for x in xs]
+                    assert None not in idx, (m, l, side)
+                    assert all(b == a - 1 for a, b in zip(idx, idx[1:])), (m, l, side)

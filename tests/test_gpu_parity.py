@@ -265,3 +265,65 @@ def test_decode_time_flat_across_masks():
         times.append(sorted(ts)[1])
         assert torch.equal(out, img), bin(m)
     assert max(times) / min(times) < 1.3, times
+
+
+TRIM_CASES = [GEOMS[1], GEOMS[2], GEOMS[3], ("tiny(6,3)", 20, 3, [-4, -1, 0, 2, 5, 6])]
+
+
+def trimmed_reference(plan, full_proj, p, P, Q):
+    """The oracle's full projections gathered into a trimmed plan's layout."""
+    offs, _, _, _ = oracle.offsets(p, P, Q)
+    cols = [offs[i] + int(plan.full_bin[t]) for i in range(len(p))
+            for t in range(plan.offsets[i], plan.offsets[i] + plan.bins[i])]
+    return np.ascontiguousarray(full_proj[:, cols])
+
+
+@pytest.mark.parametrize("name,P,Q,p", TRIM_CASES)
+def test_trimmed_plan_encode_decode(name, P, Q, p):
+    """Unused-bin removal: encode writes exactly the oracle's bins at the
+    stored positions; decode from the stored bins alone (lost projections'
+    slices junk) gives the image, for every mask (sampled at (12,8))."""
+    tr = mj.mojette_plan_ex(P, Q, p, mj.MOJETTE_PLAN_TRIM_UNUSED)
+    S = 301
+    img = inputs.stripes(S, Q, P, seed=P * Q + 7)
+    ref = trimmed_reference(tr, oracle.encode(img, p, threads=8), p, P, Q)
+    assert ref.shape == (S, tr.total)
+    assert (encode_gpu(tr, img) == ref).all()
+    n = len(p)
+    masks = [m for e in range(n - Q + 1) for m in inputs.all_masks(n, e)]
+    masks = masks if len(masks) <= 80 else masks[::11]
+    for m in masks:
+        pr = ref.copy()
+        for i in range(n):
+            if (m >> i) & 1:
+                pr[:, tr.offsets[i]: tr.offsets[i] + tr.bins[i]] = np.uint64(0xDEADBEEFDEADBEEF)
+        assert (decode_gpu(tr, pr, m) == img).all(), (name, bin(m))
+
+
+def test_trimmed_and_full_plans_in_one_batch():
+    T12 = [v for v in range(-6, 7) if v]
+    plans = [mj.mojette_plan_ex(64, 8, T12, mj.MOJETTE_PLAN_TRIM_UNUSED), mj.mojette_plan(256, 4, SIX)]
+    geo = [(64, 8, T12), (256, 4, SIX)]
+    S = [190, 70]
+    imgs, d_proj, d_out, rows = [], [], [], []
+    for k, ((P, Q, p), s) in enumerate(zip(geo, S)):
+        img = inputs.stripes(s, Q, P, seed=31 + k)
+        ref = oracle.encode(img, p, threads=8)
+        if plans[k].trimmed:
+            ref = trimmed_reference(plans[k], ref, p, P, Q)
+        imgs.append(img)
+        d_proj.append(dev(ref))
+        d_out.append(empty((s, Q, P)))
+    masks = [inputs.erasure_masks(s, len(g[2]), inputs.erasure_counts(s, len(g[2]) - g[1], seed=5), seed=6)
+             for s, g in zip(S, geo)]
+    ks = np.concatenate([np.full(s, k) for k, s in enumerate(S)])
+    src = np.concatenate([d_proj[k].data_ptr() + np.arange(s, dtype=np.uint64) * np.uint64(plans[k].total * 8)
+                          for k, s in enumerate(S)])
+    dst = np.concatenate([d_out[k].data_ptr() + np.arange(s, dtype=np.uint64) * np.uint64(geo[k][0] * geo[k][1] * 8)
+                          for k, s in enumerate(S)])
+    table = mj.stripe_table(plans, ks, mj.MOJETTE_OP_DECODE, np.concatenate(masks), src, dst)
+    b = mj.mojette_batch_create(table, plans, mj.MOJETTE_BATCH_GRAPH)
+    mj.mojette_batch_run(b)
+    torch.cuda.synchronize()
+    for k in range(2):
+        assert (host(d_out[k]) == imgs[k]).all()
