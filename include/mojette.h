@@ -333,8 +333,9 @@ typedef struct mojette_server_s *mojette_server_t;
 /*
  * mojette_server_create -- a server on the current device.
  *   device_budget_bytes  the device buffer pool, allocated here once (the
- *                        admission budget: a request holds its input and
- *                        output stripes there while it is in flight);
+ *                        admission budget: a request holds its input stripes
+ *                        in one half and its output stripes in the other
+ *                        while it is in flight);
  *   slots                waves in flight at once (1..64), each with its own
  *                        stream and batch;
  *   max_wave_stripes     stripes per wave at most (bounds a wave's latency);
@@ -350,10 +351,12 @@ int mojette_server_create(int64_t device_budget_bytes, int slots,
  * the host buffers must stay valid (and host_dst unread) until the request
  * completes. Admission: a wave takes queued requests in order while their
  * buffers fit the pool; a request that does not fit waits (later requests
- * wait behind it). Errors (nothing is queued): -EINVAL, -ENOTRECOVERABLE (a
- * read's mask leaves fewer than Q projections), -ENOSPC (a request larger
- * than the budget or than max_wave_stripes), or an error of a wave
- * launched meanwhile (see mojette_server_poll).
+ * wait behind it). A wave's requests whose host buffers follow each other
+ * exactly (and whose device buffers do too) are copied in one transfer.
+ * Errors (nothing is queued): -EINVAL, -ENOTRECOVERABLE (a read's mask
+ * leaves fewer than Q projections), -ENOSPC (a request whose input or
+ * output exceeds half the budget, or larger than max_wave_stripes), or an
+ * error of a wave launched meanwhile (see mojette_server_poll).
  */
 int mojette_server_submit(mojette_server_t server, const mojette_request_t *reqs,
                           int64_t n);

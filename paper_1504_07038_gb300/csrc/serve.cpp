@@ -7,8 +7,14 @@
 // and output in pinned host memory. The server
 //   - queues requests as they are submitted (never blocks);
 //   - admits them first-come first-served into a wave while the wave's
-//     device buffers fit the pool (the budget) and the wave stays under its
-//     stripe cap; a request waits for memory rather than being skipped;
+//     device buffers fit the pool (the budget: one half for inputs, one for
+//     outputs, each carved first-fit) and the wave stays under its stripe
+//     cap; a request waits for memory rather than being skipped;
+//   - copies a wave's inputs in and outputs out with one cudaMemcpyAsync per
+//     run of requests whose host buffers and device buffers are both
+//     back to back (first-fit keeps the device side so for a fresh pool), so
+//     requests that arrive in a contiguous host ring move in a few large
+//     copies instead of one per request;
 //   - runs every wave on its own slot: a stream, a batch (one kernel per
 //     (operation, plan), every stripe its own mask) and an event; up to
 //     `slots` waves are in flight, so one wave's copies overlap another's
@@ -30,7 +36,7 @@
 namespace mojette {
 namespace {
 
-constexpr size_t kPoolAlign = 256;
+constexpr size_t kPoolAlign = 16;   // every buffer starts 16-byte aligned
 
 // First-fit allocator over [0, size) with coalescing of free blocks.
 class Pool {
@@ -100,14 +106,14 @@ struct Slot {
 struct Server {
     int device = 0;
     char *pool_base = nullptr;
-    size_t budget = 0;
-    Pool pool;
+    size_t budget = 0, half = 0;
+    Pool pin, pout;                  // [0, half): inputs, [half, budget): outputs
     int64_t max_wave_stripes = 0;
     std::vector<Slot> slots;
     std::deque<Req> queue;
     std::vector<mojette_completion_t> ready;
     std::chrono::steady_clock::time_point t0;
-    int64_t waves = 0, completed = 0, peak_used = 0;
+    int64_t waves = 0, completed = 0, peak_used = 0, copies = 0;
     double now() const
     {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -130,8 +136,8 @@ void retire(Server &s, Slot &sl, int status)
 {
     const double t = s.now();
     for (const Req &q : sl.reqs) {
-        s.pool.release(q.in_off, q.in_bytes);
-        s.pool.release(q.out_off, q.out_bytes);
+        s.pin.release(q.in_off, q.in_bytes);
+        s.pout.release(q.out_off - s.half, q.out_bytes);
         mojette_completion_t c;
         c.id = q.r.id;
         c.status = status;
@@ -156,11 +162,12 @@ int launch_wave(Server &s, Slot &sl)
         Req &q = s.queue.front();
         if (!sl.reqs.empty() && stripes + q.r.stripes > s.max_wave_stripes) break;
         size_t in_off = 0, out_off = 0;
-        if (!s.pool.alloc(q.in_bytes, &in_off)) break;
-        if (!s.pool.alloc(q.out_bytes, &out_off)) {
-            s.pool.release(in_off, q.in_bytes);
+        if (!s.pin.alloc(q.in_bytes, &in_off)) break;
+        if (!s.pout.alloc(q.out_bytes, &out_off)) {
+            s.pin.release(in_off, q.in_bytes);
             break;
         }
+        out_off += s.half;
         q.in_off = in_off;
         q.out_off = out_off;
         q.admit = t;
@@ -169,13 +176,36 @@ int launch_wave(Server &s, Slot &sl)
         s.queue.pop_front();
     }
     if (sl.reqs.empty()) return 0;
-    s.peak_used = std::max<int64_t>(s.peak_used, (int64_t)s.pool.used());
+    s.peak_used = std::max<int64_t>(s.peak_used, (int64_t)(s.pin.used() + s.pout.used()));
     int err = 0;
-    // inputs in, one copy per request (pinned host memory)
-    for (const Req &q : sl.reqs)
-        if ((err = record_cuda(cudaMemcpyAsync(s.pool_base + q.in_off, q.r.host_src, q.in_bytes,
-                                               cudaMemcpyHostToDevice, sl.stream))))
-            return err;
+    // Copies of runs of requests whose host and device buffers both follow
+    // each other exactly (no byte outside the requested ranges is copied).
+    auto copy_runs = [&](bool in) -> int {
+        const cudaMemcpyKind kind = in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+        size_t i = 0;
+        while (i < sl.reqs.size()) {
+            const Req &q0 = sl.reqs[i];
+            char *host0 = in ? (char *)q0.r.host_src : (char *)q0.r.host_dst;
+            char *dev0 = s.pool_base + (in ? q0.in_off : q0.out_off);
+            size_t len = in ? q0.in_bytes : q0.out_bytes;
+            size_t j = i + 1;
+            for (; j < sl.reqs.size(); ++j) {
+                const Req &qj = sl.reqs[j];
+                char *hj = in ? (char *)qj.r.host_src : (char *)qj.r.host_dst;
+                char *dj = s.pool_base + (in ? qj.in_off : qj.out_off);
+                if (hj != host0 + len || dj != dev0 + len) break;
+                len += in ? qj.in_bytes : qj.out_bytes;
+            }
+            const int e = in ? record_cuda(cudaMemcpyAsync(dev0, host0, len, kind, sl.stream))
+                             : record_cuda(cudaMemcpyAsync(host0, dev0, len, kind, sl.stream));
+            if (e) return e;
+            ++s.copies;
+            i = j;
+        }
+        return 0;
+    };
+    // inputs in (pinned host memory)
+    if ((err = copy_runs(true))) return err;
     // one stripe table over the wave
     sl.table.clear();
     sl.table.reserve((size_t)stripes);
@@ -201,11 +231,8 @@ int launch_wave(Server &s, Slot &sl)
         return err;
     }
     if ((err = mojette_batch_run(sl.batch, (mojette_stream_t)sl.stream))) return err;
-    // outputs back, one copy per request
-    for (const Req &q : sl.reqs)
-        if ((err = record_cuda(cudaMemcpyAsync(q.r.host_dst, s.pool_base + q.out_off, q.out_bytes,
-                                               cudaMemcpyDeviceToHost, sl.stream))))
-            return err;
+    // outputs back
+    if ((err = copy_runs(false))) return err;
     if ((err = record_cuda(cudaEventRecord(sl.done, sl.stream)))) return err;
     sl.busy = true;
     ++s.waves;
@@ -273,6 +300,7 @@ int mojette_server_create(int64_t device_budget_bytes, int slots, int64_t max_wa
     if (!s) return -ENOMEM;
     s->t0 = std::chrono::steady_clock::now();
     s->budget = (size_t)device_budget_bytes & ~(kPoolAlign - 1);
+    s->half = (s->budget / 2) & ~(kPoolAlign - 1);
     s->max_wave_stripes = max_wave_stripes;
     int err = record_cuda(cudaGetDevice(&s->device));
     if (!err) {
@@ -283,7 +311,8 @@ int mojette_server_create(int64_t device_budget_bytes, int slots, int64_t max_wa
             err = e == cudaErrorMemoryAllocation ? -ENOMEM : -EIO;
         }
     }
-    s->pool.reset(err ? 0 : s->budget);
+    s->pin.reset(err ? 0 : s->half);
+    s->pout.reset(err ? 0 : s->budget - s->half);
     s->slots.resize((size_t)slots);
     for (Slot &sl : s->slots) {
         if (err) break;
@@ -316,8 +345,9 @@ int mojette_server_submit(mojette_server_t server, const mojette_request_t *reqs
         }
         size_t in = 0, out = 0;
         request_bytes(r, &in, &out);
-        const size_t need = ((in + kPoolAlign - 1) & ~(kPoolAlign - 1)) + ((out + kPoolAlign - 1) & ~(kPoolAlign - 1));
-        if (need > s->budget || r.stripes > s->max_wave_stripes) return -ENOSPC;
+        const size_t rin = (in + kPoolAlign - 1) & ~(kPoolAlign - 1);
+        const size_t rout = (out + kPoolAlign - 1) & ~(kPoolAlign - 1);
+        if (rin > s->half || rout > s->budget - s->half || r.stripes > s->max_wave_stripes) return -ENOSPC;
     }
     const double t = s->now();
     for (int64_t i = 0; i < n; ++i) {
@@ -360,7 +390,7 @@ int mojette_server_stats(mojette_server_t server, int64_t *queued, int64_t *in_f
     if (in_flight) *in_flight = fl;
     if (waves) *waves = s->waves;
     if (completed) *completed = s->completed;
-    if (pool_used) *pool_used = (int64_t)s->pool.used();
+    if (pool_used) *pool_used = (int64_t)(s->pin.used() + s->pout.used());
     if (pool_peak) *pool_peak = s->peak_used;
     return 0;
 }

@@ -59,8 +59,9 @@ class Workload:
             e = inputs.erasure_counts(len(sel), n_p - Q, seed=seed + k)
             masks[sel] = inputs.erasure_masks(len(sel), n_p, e, seed=seed + 31 * k)
         self.stripes, self.write, self.geom = stripes, write, g
-        # pinned arenas, 256-byte aligned slices
-        al = lambda x: (x + 255) // 256 * 256
+        # pinned arenas, slices back to back (16-byte aligned), as a
+        # receive ring would hold them
+        al = lambda x: (x + 15) // 16 * 16
         in_off = np.concatenate([[0], np.cumsum(al(in_bytes))[:-1]])
         out_off = np.concatenate([[0], np.cumsum(al(out_bytes))[:-1]])
         self.h_in = torch.empty(int(al(in_bytes).sum()) // 8, dtype=torch.int64).pin_memory()

@@ -80,7 +80,8 @@ def test_poisson_arrivals(wl):
 
 def test_one_request_at_a_time_budget(wl):
     # room for the largest request only: waves of one request, still drains
-    need = int(max(((wl.in_bytes + 255) // 256 + (wl.out_bytes + 255) // 256) * 256))
+    # each half of the pool holds the largest input / output
+    need = 2 * int(max(max((wl.in_bytes + 15) // 16), max((wl.out_bytes + 15) // 16)) * 16)
     srv = mj.mojette_server_create(need, slots=2, max_wave_stripes=1 << 20)
     wl.clear_outputs()
     order = np.arange(0, len(wl), 4)
