@@ -113,7 +113,7 @@ struct Server {
     std::deque<Req> queue;
     std::vector<mojette_completion_t> ready;
     std::chrono::steady_clock::time_point t0;
-    int64_t waves = 0, completed = 0, peak_used = 0, copies = 0;
+    int64_t waves = 0, completed = 0, peak_used = 0;
     double now() const
     {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -199,7 +199,6 @@ int launch_wave(Server &s, Slot &sl)
             const int e = in ? record_cuda(cudaMemcpyAsync(dev0, host0, len, kind, sl.stream))
                              : record_cuda(cudaMemcpyAsync(host0, dev0, len, kind, sl.stream));
             if (e) return e;
-            ++s.copies;
             i = j;
         }
         return 0;
