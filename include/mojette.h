@@ -100,6 +100,23 @@ int mojette_plan_ex(int P, int Q, const int *p, int n, uint32_t flags,
  */
 int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin);
 
+/*
+ * mojette_plan_config -- read (get, may be NULL) and then install (set, may
+ * be NULL) the launch configuration batches of this plan use, as
+ * mojette_batch_tune leaves it (so a tuned configuration can be saved and
+ * restored across processes). 8 words each:
+ *   [0] 1: decode configuration set (tuned), 0: library defaults;
+ *   [1] decode kernel (0 decode_lines, 1 decode_fronts, 2 decode_stream,
+ *       3 decode_cols; Q > 8 allows 1 only);
+ *   [2] work items per CTA (1 .. 64); [3] persistent grid (0/1);
+ *   [4] decode_lines row phases (0/1);
+ *   [5] 1: encode configuration set; [6] encode tile bytes (0: by Q);
+ *   [7] reserved, 0.
+ * Batches built after the call use it. Errors: -EINVAL (NULL plan, a value
+ * out of range).
+ */
+int mojette_plan_config(mojette_plan_t plan, int32_t *get, const int32_t *set);
+
 /* Release a plan and every host and device resource it holds. Must not be
  * called while work that uses the plan is still in flight. NULL is a no-op. */
 int mojette_plan_destroy(mojette_plan_t plan);

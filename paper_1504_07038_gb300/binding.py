@@ -50,6 +50,7 @@ def lib():
             L.mojette_plan_destroy.argtypes = [_PTR]
             L.mojette_plan_ex.argtypes = [_INT, _INT, _PTR, _INT, _U32, ctypes.POINTER(_PTR)]
             L.mojette_plan_bins.argtypes = [_PTR, _PTR]
+            L.mojette_plan_config.argtypes = [_PTR, _PTR, _PTR]
             L.mojette_plan_info.argtypes = [_PTR, _PTR, _PTR, _PTR]
             L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
@@ -71,7 +72,8 @@ def lib():
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
             L.mojette_last_cuda_error.argtypes = []
-            for name in ("mojette_plan", "mojette_plan_ex", "mojette_plan_bins", "mojette_plan_destroy",
+            for name in ("mojette_plan", "mojette_plan_ex", "mojette_plan_bins", "mojette_plan_config",
+                         "mojette_plan_destroy",
                          "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc",
                          "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
@@ -177,6 +179,58 @@ def mojette_plan_ex(P: int, Q: int, p, flags: int = 0) -> Plan:
 
 def mojette_plan_destroy(plan: Plan) -> None:
     plan.close()
+
+
+_CONFIG_KEYS = ("decode_tuned", "decode_kernel", "decode_gpc", "decode_persist", "decode_rowoff",
+                "encode_tuned", "encode_tile_bytes", "reserved")
+
+
+def mojette_plan_config(plan: Plan, config: dict | None = None) -> dict:
+    """The plan's batch launch configuration as a dict; with ``config``,
+    install that one first (keys as returned; missing keys keep their value)."""
+    cur = np.zeros(8, dtype=np.int32)
+    _check(lib().mojette_plan_config(plan.handle, cur.ctypes.data, None), "mojette_plan_config")
+    if config is not None:
+        new = cur.copy()
+        for k, v in config.items():
+            new[_CONFIG_KEYS.index(k)] = int(v)
+        _check(lib().mojette_plan_config(plan.handle, None, new.ctypes.data), "mojette_plan_config")
+        cur = new
+    return {k: int(v) for k, v in zip(_CONFIG_KEYS, cur) if k != "reserved"}
+
+
+def geometry_key(plan: Plan) -> str:
+    return f"P{plan.P}-Q{plan.Q}-p{','.join(str(v) for v in plan.p)}" + ("-trimmed" if plan.trimmed else "")
+
+
+def save_tuning(plans, path: str) -> None:
+    """Write the launch configurations of ``plans`` to a JSON file keyed by
+    geometry (merged into the file's existing entries)."""
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    for pl in plans:
+        data[geometry_key(pl)] = mojette_plan_config(pl)
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+
+
+def load_tuning(plans, path: str) -> int:
+    """Install the configurations stored for ``plans``' geometries; returns
+    how many plans had one."""
+    import json
+    with open(path) as f:
+        data = json.load(f)
+    n = 0
+    for pl in plans:
+        cfg = data.get(geometry_key(pl))
+        if cfg:
+            mojette_plan_config(pl, cfg)
+            n += 1
+    return n
 
 
 def mojette_plan_info(plan: Plan):

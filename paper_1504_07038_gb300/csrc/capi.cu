@@ -113,6 +113,39 @@ int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin)
     return pl->trimmed ? 1 : 0;
 }
 
+int mojette_plan_config(mojette_plan_t plan, int32_t *get, const int32_t *set)
+{
+    if (!plan) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    std::lock_guard<std::mutex> g(pl->mu);
+    if (get) {
+        get[0] = pl->tuned_dec ? 1 : 0;
+        get[1] = pl->dec_cfg.kernel;
+        get[2] = pl->dec_cfg.gpc;
+        get[3] = pl->dec_cfg.persist;
+        get[4] = pl->dec_cfg.rowoff;
+        get[5] = pl->tuned_enc ? 1 : 0;
+        get[6] = pl->enc_cfg.tile_bytes;
+        get[7] = 0;
+    }
+    if (set) {
+        if (set[0]) {
+            if (set[1] < 0 || set[1] > 3 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
+                return -EINVAL;
+            if (set[1] != 1 && pl->Q > 8) return -EINVAL;
+            pl->dec_cfg.kernel = set[1];
+            pl->dec_cfg.gpc = set[2];
+            pl->dec_cfg.persist = set[3];
+            pl->dec_cfg.rowoff = set[4];
+        }
+        pl->tuned_dec = set[0] != 0;
+        if (set[5] && set[6] < 0) return -EINVAL;
+        if (set[5]) pl->enc_cfg.tile_bytes = set[6];
+        pl->tuned_enc = set[5] != 0;
+    }
+    return 0;
+}
+
 int mojette_plan_destroy(mojette_plan_t plan)
 {
     if (!plan) return 0;

@@ -200,3 +200,23 @@ def test_trimmed_plan_keeps_every_bin_a_path_reads(P, Q, p):
                     idx = [where[i].get(l * p[i] - x - bmin) for x in xs]
                     assert None not in idx, (m, l, side)
                     assert all(b == a - 1 for a, b in zip(idx, idx[1:])), (m, l, side)
+
+
+def test_plan_config_round_trip(tmp_path):
+    """Tuned launch configurations can be read, installed and kept in a JSON
+    file keyed by geometry (host only)."""
+    from paper_1504_07038_gb300 import binding as mj
+    a = mj.mojette_plan(256, 4, [-3, -2, -1, 1, 2, 3])
+    b = mj.mojette_plan(64, 8, [v for v in range(-6, 7) if v])
+    assert mj.mojette_plan_config(a)["decode_tuned"] == 0
+    mj.mojette_plan_config(a, {"decode_tuned": 1, "decode_kernel": 3, "decode_gpc": 2,
+                               "encode_tuned": 1, "encode_tile_bytes": 16000})
+    path = str(tmp_path / "tuning.json")
+    mj.save_tuning([a, b], path)
+    a2 = mj.mojette_plan(256, 4, [-3, -2, -1, 1, 2, 3])
+    assert mj.load_tuning([a2], path) == 1
+    c = mj.mojette_plan_config(a2)
+    assert (c["decode_tuned"], c["decode_kernel"], c["decode_gpc"], c["encode_tile_bytes"]) == (1, 3, 2, 16000)
+    with pytest.raises(mj.MojetteError) as ei:
+        mj.mojette_plan_config(b, {"decode_tuned": 1, "decode_kernel": 0, "decode_gpc": 0})
+    assert ei.value.code == -errno.EINVAL
