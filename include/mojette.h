@@ -149,7 +149,10 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
  *   erasure_mask  bit i set: projection i is lost;
  *   d_img         [S][Q][P] uint64 pixels, written.
  * At least Q projections must survive, and Q <= MOJETTE_MAX_DECODE_LINES;
- * otherwise -ENOTRECOVERABLE (resp. -EINVAL). The reconstruction path for
+ * otherwise -ENOTRECOVERABLE (resp. -EINVAL). A stripe is rebuilt in shared
+ * memory: its Q * P words plus zero columns must fit in one CTA's (about
+ * 28000 words, e.g. 16 KB-wide lines at Q = 4); larger stripes get -EINVAL
+ * before any launch (cut objects into smaller stripes). The reconstruction path for
  * the surviving set is computed on the host on first use and cached in the
  * plan (the paper's pre-determined path, Sec. 2.2 and Sec. 3.1).
  * Errors: -EINVAL, -ERANGE, -ENOTRECOVERABLE, -ENOMEM, -EIO.

@@ -363,9 +363,13 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         if (k.op == MOJETTE_OP_DECODE) {
             DecodeLayout L;
             if ((err = class_layout(k, k.dcfg, &L))) {
-                // a tuned configuration that no longer fits: the defaults
+                // a tuned configuration that no longer fits: the defaults,
+                // else decode_fronts (G down to one stripe)
                 k.dcfg = DecodeConfig();
-                if ((err = class_layout(k, k.dcfg, &L))) return err;
+                if ((err = class_layout(k, k.dcfg, &L))) {
+                    k.dcfg.kernel = 1;
+                    if ((err = class_layout(k, k.dcfg, &L))) return err;
+                }
             }
             if ((err = fill_work(b, k, L.G))) return err;
         }

@@ -144,6 +144,12 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;
     DecodeLayout L;
     int err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
+    if (err == -EINVAL && cfg.kernel != 1) {
+        // a warp's G stripes do not fit in shared memory: decode_fronts sizes
+        // G to what fits, down to one stripe
+        cfg.kernel = 1;
+        err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
+    }
     if (err) return err;
     return launch_decode_kernel<false>(a, L, cfg, (d.S + L.G - 1) / L.G, st);
 }

@@ -8,6 +8,8 @@ geometries), and at the full benchmark sizes on sampled stripes plus the
 size-independent property decode(encode(img)) == img on every stripe.
 Integer XOR work: the tolerance is zero.
 """
+import errno
+
 import numpy as np
 import pytest
 
@@ -327,3 +329,29 @@ def test_trimmed_and_full_plans_in_one_batch():
     torch.cuda.synchronize()
     for k in range(2):
         assert (host(d_out[k]) == imgs[k]).all()
+
+
+@pytest.mark.parametrize("P,Q,p", [(2048, 4, SIX), (4096, 4, SIX), (1024, 8, TWELVE), (6000, 2, [-1, 1, 2])])
+def test_large_stripes(P, Q, p):
+    """Stripes far above the paper's blocks (16 KB to 94 KB): encode stages
+    one stripe per tile, decode runs one or a few stripes per warp."""
+    S = 37
+    img = inputs.stripes(S, Q, P, seed=P + Q)
+    plan = mj.mojette_plan(P, Q, p)
+    proj = oracle.encode(img, p, threads=8)
+    assert (encode_gpu(plan, img) == proj).all()
+    n = len(p)
+    for m in inputs.all_masks(n, n - Q)[:4] + [0]:
+        assert (decode_gpu(plan, proj, m) == img).all(), (P, Q, bin(m))
+
+
+def test_stripe_beyond_shared_memory_refused():
+    """A stripe whose words cannot fit in one CTA's shared memory is refused
+    before any launch."""
+    P, Q, p = 16384, 4, SIX
+    plan = mj.mojette_plan(P, Q, p)
+    buf = empty((2, plan.total))
+    out = empty((2, Q, P))
+    with pytest.raises(mj.MojetteError) as ei:
+        mj.mojette_decode(plan, buf, 0b000011, out, 2)
+    assert ei.value.code == -errno.EINVAL
