@@ -412,6 +412,16 @@ int mojette_server_destroy(mojette_server_t server);
  */
 int mojette_device_status(uint32_t *flags, int clear);
 
+/*
+ * mojette_selftest_wait -- failure-detection self-test (no counterpart in
+ * the paper): enqueue on `stream` one warp that waits, through the bounded
+ * mbarrier wait the encoder uses for its copies, for bytes that are never
+ * sent. After limit_ns (1 us .. 1 s) the wait gives up, the kernel sets
+ * status bit 0 and returns: a following mojette_device_status returns
+ * -ETIMEDOUT, and the device stays usable. Errors: -EINVAL, -EIO.
+ */
+int mojette_selftest_wait(int64_t limit_ns, mojette_stream_t stream);
+
 /* Text for a status code returned by any call above. */
 const char *mojette_strerror(int status);
 

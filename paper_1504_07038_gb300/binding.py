@@ -68,6 +68,7 @@ def lib():
             L.mojette_server_now.argtypes = [_PTR, ctypes.POINTER(ctypes.c_double)]
             L.mojette_server_stats.argtypes = [_PTR] + [ctypes.POINTER(_I64)] * 6
             L.mojette_server_destroy.argtypes = [_PTR]
+            L.mojette_selftest_wait.argtypes = [_I64, _PTR]
             L.mojette_device_status.argtypes = [ctypes.POINTER(_U32), _INT]
             L.mojette_strerror.argtypes = [_INT]
             L.mojette_strerror.restype = ctypes.c_char_p
@@ -81,7 +82,7 @@ def lib():
                          "mojette_batch_destroy", "mojette_server_create", "mojette_server_submit",
                          "mojette_server_poll", "mojette_server_now", "mojette_server_stats",
                          "mojette_server_destroy",
-                         "mojette_device_status", "mojette_last_cuda_error"):
+                         "mojette_selftest_wait", "mojette_device_status", "mojette_last_cuda_error"):
                 getattr(L, name).restype = _INT
             _lib = L
     return _lib
@@ -449,6 +450,12 @@ def mojette_server_stats(server: Server) -> dict:
 
 def mojette_server_destroy(server: Server) -> None:
     server.close()
+
+
+def mojette_selftest_wait(limit_ns: int = 20_000_000, stream=None) -> None:
+    """Enqueue the bounded-wait self-test (mojette_device_status then reports
+    -ETIMEDOUT)."""
+    _check(lib().mojette_selftest_wait(int(limit_ns), _stream(stream)), "mojette_selftest_wait")
 
 
 def mojette_device_status(clear: bool = True) -> int:

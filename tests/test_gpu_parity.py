@@ -355,3 +355,20 @@ def test_stripe_beyond_shared_memory_refused():
     with pytest.raises(mj.MojetteError) as ei:
         mj.mojette_decode(plan, buf, 0b000011, out, 2)
     assert ei.value.code == -errno.EINVAL
+
+
+def test_bounded_wait_reports_timeout():
+    """Failure detection without a fault: a wait that nothing completes gives
+    up after its limit, the status word says so (-ETIMEDOUT), the status is
+    cleared, and the device still computes correctly."""
+    mj.mojette_selftest_wait(20_000_000)
+    with pytest.raises(mj.MojetteError) as ei:
+        mj.mojette_device_status(clear=True)
+    assert ei.value.code == -errno.ETIMEDOUT
+    assert mj.mojette_device_status(clear=True) == 0
+    P, Q, p = 128, 4, SIX
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(9, Q, P, seed=2)
+    proj = oracle.encode(img, p)
+    assert (encode_gpu(plan, img) == proj).all()
+    assert (decode_gpu(plan, proj, 0b000101) == img).all()
