@@ -358,7 +358,7 @@ def run_gpu(args, w):
     return line
 
 
-def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream, chunks: int = 8):
+def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
     """Same metric through the C ABI with host buffers: every step copies the
     image in and the projections out (encode), then for each mask the
     projection block in (decode reads only the surviving slices of it) and
@@ -375,14 +375,15 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream, chunks: i
     h_proj = torch.empty((S, plan.total), dtype=torch.int64).pin_memory()
     h_out = torch.empty((S, Q, P), dtype=torch.int64).pin_memory()
     d_in = torch.full((S, plan.total), 0x0BAD0BAD0BAD0BAD, dtype=torch.int64, device="cuda")
-    side = [torch.cuda.Stream(), torch.cuda.Stream()]
+    chunks, nstreams = args.e2e_chunks, args.e2e_streams
+    side = [torch.cuda.Stream() for _ in range(nstreams)]
     bounds = [(S * c // chunks, S * (c + 1) // chunks) for c in range(chunks)]
 
     def step():
         for st in side:
             st.wait_stream(stream)
         for c, (a, b) in enumerate(bounds):
-            st = side[c % 2]
+            st = side[c % nstreams]
             with torch.cuda.stream(st):
                 d_img[a:b].copy_(h_img[a:b], non_blocking=True)
                 mj.mojette_encode(plan, d_img[a:b], d_proj[a:b], b - a, st)
@@ -411,7 +412,7 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream, chunks: i
             "h2d_bytes_per_step": S * Q * P * 8 + len(masks) * S * plan.total * 8,
             "d2h_bytes_per_step": S * plan.total * 8 + len(masks) * S * Q * P * 8,
             "ms_per_step": round(ms, 3), "steps": steps, "round_trip_ok": ok,
-            "pipeline": f"{chunks} stripe slices over 2 streams"}
+            "pipeline": f"{chunks} stripe slices over {nstreams} streams"}
 
 
 # ------------------------------------------------------------ batched arm --
@@ -627,6 +628,8 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the request-server measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=inputs.DEFAULT_SEED, help="seed of the stripe pixels")
+    ap.add_argument("--e2e-chunks", type=int, default=8, help="stripe slices of the e2e pipeline")
+    ap.add_argument("--e2e-streams", type=int, default=2, help="streams of the e2e pipeline")
     ap.add_argument("--stripes", type=int, default=0, help="override the workload's stripe count")
     args = ap.parse_args()
     if args.warmup < 3:
