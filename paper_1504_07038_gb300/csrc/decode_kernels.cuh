@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     int dk[Q > 2 ? Q - 2 : 1];
     uint32_t sfw = 0u;
     uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    int chain = 0;   // steady steps: lines l+1 .. l+chain are linked to this one
     auto load_group = [&](const DecGroup &gr) {
         const int T = gr.T;
         T4 = (T + 3) & ~3;
@@ -384,6 +385,9 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
 #pragma unroll
         for (int k = 1; k < Q - 1; ++k) dk[k - 1] = off((l + 1 + k) % Q);
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
+        chain = 0;
+        if (ok)
+            for (int j = l; j + 1 < Q && ((gr.fwd >> (2 * j + side)) & 1u); ++j) ++chain;
         uint32_t c[Q];
 #pragma unroll
         for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
@@ -459,10 +463,21 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
 #pragma unroll
                 for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
                 if (Q > 1) v ^= ld_s64_if(pos + d0, (sfw & has_next) ^ 1u);
+                if constexpr (Q <= 4) {
+                    // the linked lines' own values, all fetched at once: one
+                    // shuffle latency instead of log2 Q dependent rounds
+                    const uint64_t x = v;
 #pragma unroll
-                for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
-                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
-                    if (slink[r]) v ^= tv;
+                    for (int d = 1; d < Q; ++d) {
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x, 2 * d * G);
+                        if (d <= chain) v ^= tv;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                        if (slink[r]) v ^= tv;
+                    }
                 }
                 st_s64_if(pos, v, ok);
                 pos += stepb;
