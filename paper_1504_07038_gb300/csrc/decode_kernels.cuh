@@ -37,6 +37,8 @@
 #include <cerrno>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "ptx.cuh"
 
@@ -1015,15 +1017,33 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     if ((err = record_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)L.smem))))
         return err;
-    int64_t grid = (nitems + a.gpc - 1) / a.gpc;
-    if (a.persist) {
+    // CTAs the device holds at once for this kernel and shared memory
+    // (cached: the query costs host time on every launch otherwise)
+    int slots = 0;
+    {
+        static std::mutex mu;
+        static std::map<std::pair<const void *, int64_t>, int> cache;
         int dev = 0, sms = 0, per_sm = 0;
         if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
-        if ((err = record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return err;
-        if ((err = record_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32, (size_t)L.smem))))
-            return err;
-        grid = std::min<int64_t>(grid, (int64_t)std::max(per_sm, 1) * sms);
+        const auto key = std::make_pair((const void *)fn, L.smem * 64 + dev);
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            slots = it->second;
+        } else {
+            if ((err = record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return err;
+            if ((err = record_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32, (size_t)L.smem))))
+                return err;
+            slots = std::max(per_sm, 1) * sms;
+            cache[key] = slots;
+        }
     }
+    // a launch with fewer items than the device holds runs them all at once
+    // (fewer items per CTA) instead of leaving SMs idle
+    if (!a.persist && nitems < (int64_t)slots * a.gpc)
+        a.gpc = (int)std::max<int64_t>(1, (nitems + slots - 1) / slots);
+    int64_t grid = (nitems + a.gpc - 1) / a.gpc;
+    if (a.persist) grid = std::min<int64_t>(grid, (int64_t)slots);
     fn<<<(unsigned)grid, 32, (size_t)L.smem, st>>>(a);
     return record_cuda(cudaGetLastError());
 }
