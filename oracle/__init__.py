@@ -13,6 +13,10 @@ this module only marshals numpy arrays. Functions follow the paper:
 * ``katz``        -- the reconstruction criterion, Eq. 3.
 * ``encode``      -- forward Mojette transform, Eq. 1 (XOR addition, Sec. 3).
 * ``decode``      -- inverse Mojette transform by peeling, Sec. 2.2.
+* ``sys_decode``  -- the systematic form (data lines are packets, parity
+  packets are projections; mentioned in Sec. 2.3 and Sec. 4, not defined
+  there): surviving lines copied and removed from the parity bins, the lost
+  lines peeled as in Sec. 2.2.
 
 Layout: images are ``uint64[S, Q, P]`` (row l = data line, x = column);
 projections are ``uint64[S, sum_i B_i]`` with projection i at offset
@@ -85,6 +89,9 @@ def _load():
             lib.oracle_decode.restype = _INT
             lib.oracle_decode.argtypes = [_INT, _INT, _PTR, _INT, _PTR, _PTR,
                                           _I64, _PTR, _I64, _INT]
+            lib.oracle_sys_decode.restype = _INT
+            lib.oracle_sys_decode.argtypes = [_INT, _INT, _PTR, _INT, _PTR, _PTR,
+                                              _PTR, _I64, _PTR, _I64, _INT]
             _lib = lib
     return _lib
 
@@ -168,4 +175,35 @@ def decode(proj: np.ndarray, p, P: int, Q: int, masks, threads: int = 1) -> np.n
                               S, m.ctypes.data_as(_PTR), len(m), int(threads))
     if r < 0:
         raise OracleError(r, "decode")
+    return out
+
+
+def sys_decode(data: np.ndarray, parity: np.ndarray, p, P: int, Q: int, masks,
+               threads: int = 1) -> np.ndarray:
+    """Systematic decode -> uint64[S, Q, P].
+
+    ``data`` (uint64[S, Q, P]) holds the data lines as received (lost lines
+    are never read); ``parity`` (uint64[S, total]) the projections along
+    ``p``. Mask bit l < Q: data line l lost; bit Q + i: projection i lost.
+    Raises OracleError(-ENOTRECOVERABLE) when the peeling stalls.
+    """
+    data = np.ascontiguousarray(data, dtype=np.uint64)
+    parity = np.ascontiguousarray(parity, dtype=np.uint64)
+    if data.ndim == 2:
+        data = data[None]
+    if parity.ndim == 1:
+        parity = parity[None]
+    S = data.shape[0]
+    if data.shape != (S, Q, P) or parity.shape != (S, total_bins(p, P, Q)):
+        raise ValueError("buffers do not match the geometry")
+    arr, ptr = _dirs(p)
+    m = np.ascontiguousarray(np.atleast_1d(np.asarray(masks, dtype=np.uint64))
+                             .astype(np.uint32))
+    out = np.empty((S, Q, P), dtype=np.uint64)
+    r = _load().oracle_sys_decode(int(P), int(Q), ptr, len(arr),
+                                  data.ctypes.data_as(_PTR), parity.ctypes.data_as(_PTR),
+                                  out.ctypes.data_as(_PTR), S, m.ctypes.data_as(_PTR),
+                                  len(m), int(threads))
+    if r < 0:
+        raise OracleError(r, "sys_decode")
     return out

@@ -122,50 +122,27 @@ static void make_layout(int P, int Q, const int *p, int n, struct layout *L)
 }
 
 /*
- * Inverse Mojette transform of one stripe (Sec. 2.2, "Inverse Mojette
- * Algorithm"), with every surviving projection taking part:
- *   - a bin is reconstructible when exactly one of its pixels is unknown;
+ * Peeling loop of the inverse Mojette transform (Sec. 2.2, "Inverse Mojette
+ * Algorithm"), shared by both decoders below. On entry w holds the working
+ * bins of the surviving projections (known pixels already removed), cnt the
+ * number of unknown pixels in each bin, known the pixels already known, and
+ * queue[0, tail) the bins with exactly one unknown pixel. Then, until
+ * `want` pixels have been found:
+ *   - a bin with exactly one unknown pixel is reconstructible;
  *   - its value is written to that pixel (back-projection);
- *   - the pixel's contribution is then removed (XOR) from the bin it falls
- *     in, in every surviving projection, which may make further bins
- *     reconstructible;
- *   - repeat until the image is complete.
- * Reconstructible bins are taken first-in first-out. Returns
- * -ENOTRECOVERABLE if no bin is reconstructible while pixels are unknown.
- * Work buffers are supplied by the caller (sized by the layout).
+ *   - the pixel's contribution is removed (XOR) from the bin it falls in,
+ *     in every surviving projection, which may make further bins
+ *     reconstructible.
+ * Reconstructible bins are taken first-in first-out. Returns the number of
+ * pixels found, or -ENOTRECOVERABLE if the counts fall out of step (a bug).
  */
-static int decode_one(int P, int Q, const int *p, int n, const struct layout *L,
-                      uint32_t mask, const uint64_t *proj, uint64_t *img,
-                      uint64_t *w, int32_t *cnt, uint8_t *known, int64_t *queue,
-                      uint8_t *pid)
+static int64_t peel(int P, int Q, const int *p, int n, const struct layout *L,
+                    uint32_t pmask, uint64_t *img, uint64_t *w, int32_t *cnt,
+                    uint8_t *known, int64_t *queue, int64_t tail,
+                    const uint8_t *pid, int64_t want)
 {
-    const int64_t total = L->total;
-    const int64_t npix = (int64_t)P * Q;
-
-    /* working copies of the surviving bins and their unknown-pixel counts */
-    for (int i = 0; i < n; ++i)
-        for (int64_t j = 0; j < L->bins[i]; ++j) {
-            w[L->off[i] + j] = (mask >> i & 1u) ? 0 : proj[L->off[i] + j];
-            cnt[L->off[i] + j] = 0;
-            pid[L->off[i] + j] = (uint8_t)i;
-        }
-    for (int i = 0; i < n; ++i) {
-        if (mask >> i & 1u) continue;
-        for (int l = 0; l < Q; ++l)
-            for (int x = 0; x < P; ++x)
-                cnt[L->off[i] + ((int64_t)l * p[i] - x - L->bmin[i])] += 1;
-    }
-    memset(known, 0, (size_t)npix);
-
-    int64_t head = 0, tail = 0;
-    for (int i = 0; i < n; ++i) {
-        if (mask >> i & 1u) continue;
-        for (int64_t j = 0; j < L->bins[i]; ++j)
-            if (cnt[L->off[i] + j] == 1) queue[tail++] = L->off[i] + j;
-    }
-
-    int64_t found = 0;
-    while (head < tail && found < npix) {
+    int64_t head = 0, found = 0;
+    while (head < tail && found < want) {
         int64_t t = queue[head++];
         if (cnt[t] != 1) continue;
         int i = pid[t];
@@ -184,14 +161,109 @@ static int decode_one(int P, int Q, const int *p, int n, const struct layout *L,
         known[(int64_t)lu * P + xu] = 1;
         found += 1;
         for (int i2 = 0; i2 < n; ++i2) {
-            if (mask >> i2 & 1u) continue;
+            if (pmask >> i2 & 1u) continue;
             int64_t t2 = L->off[i2] + ((int64_t)lu * p[i2] - xu - L->bmin[i2]);
             w[t2] ^= v;
             cnt[t2] -= 1;
             if (cnt[t2] == 1) queue[tail++] = t2;
         }
     }
+    return found;
+}
+
+/*
+ * Inverse Mojette transform of one stripe (Sec. 2.2) with every surviving
+ * projection taking part: all pixels start unknown, the working bins are
+ * the surviving projections as stored, then peel(). Returns
+ * -ENOTRECOVERABLE if no bin is reconstructible while pixels are unknown.
+ * Work buffers are supplied by the caller (sized by the layout).
+ */
+static int decode_one(int P, int Q, const int *p, int n, const struct layout *L,
+                      uint32_t mask, const uint64_t *proj, uint64_t *img,
+                      uint64_t *w, int32_t *cnt, uint8_t *known, int64_t *queue,
+                      uint8_t *pid)
+{
+    const int64_t npix = (int64_t)P * Q;
+
+    /* working copies of the surviving bins and their unknown-pixel counts */
+    for (int i = 0; i < n; ++i)
+        for (int64_t j = 0; j < L->bins[i]; ++j) {
+            w[L->off[i] + j] = (mask >> i & 1u) ? 0 : proj[L->off[i] + j];
+            cnt[L->off[i] + j] = 0;
+            pid[L->off[i] + j] = (uint8_t)i;
+        }
+    for (int i = 0; i < n; ++i) {
+        if (mask >> i & 1u) continue;
+        for (int l = 0; l < Q; ++l)
+            for (int x = 0; x < P; ++x)
+                cnt[L->off[i] + ((int64_t)l * p[i] - x - L->bmin[i])] += 1;
+    }
+    memset(known, 0, (size_t)npix);
+
+    int64_t tail = 0;
+    for (int i = 0; i < n; ++i) {
+        if (mask >> i & 1u) continue;
+        for (int64_t j = 0; j < L->bins[i]; ++j)
+            if (cnt[L->off[i] + j] == 1) queue[tail++] = L->off[i] + j;
+    }
+    int64_t found = peel(P, Q, p, n, L, mask, img, w, cnt, known, queue, tail, pid, npix);
+    if (found < 0) return (int)found;
     return found == npix ? 0 : -ENOTRECOVERABLE;
+}
+
+/*
+ * Systematic form of the code (the paper mentions it in Sec. 2.3 and Sec. 4
+ * without defining it; this is the reading used throughout): the Q data
+ * lines are themselves Q of the packets, and r parity packets are the
+ * projections of the whole image along the r directions p[0..r-1] (Eq. 1).
+ * Erasure mask bit l (l < Q) marks data line l lost, bit Q + i parity
+ * projection i lost. Decoding copies the surviving lines, removes (XOR)
+ * their pixels from the surviving projections -- Eq. 1's sum over the
+ * known pixels -- and peels the lost lines as in Sec. 2.2. With no line
+ * lost it is a copy. Returns -ENOTRECOVERABLE if the peeling stalls.
+ */
+static int sys_decode_one(int P, int Q, const int *p, int r, const struct layout *L,
+                          uint32_t mask, const uint64_t *data, const uint64_t *parity,
+                          uint64_t *img, uint64_t *w, int32_t *cnt, uint8_t *known,
+                          int64_t *queue, uint8_t *pid)
+{
+    const uint32_t pmask = mask >> Q;     /* parity projection i lost: bit i */
+    int64_t unknown = 0;
+    for (int l = 0; l < Q; ++l) {
+        const int lost = (int)(mask >> l & 1u);
+        for (int x = 0; x < P; ++x) {
+            const int64_t k = (int64_t)l * P + x;
+            known[k] = (uint8_t)!lost;
+            img[k] = lost ? 0 : data[k];
+        }
+        if (lost) unknown += P;
+    }
+    if (unknown == 0) return 0;
+
+    for (int i = 0; i < r; ++i)
+        for (int64_t j = 0; j < L->bins[i]; ++j) {
+            w[L->off[i] + j] = (pmask >> i & 1u) ? 0 : parity[L->off[i] + j];
+            cnt[L->off[i] + j] = 0;
+            pid[L->off[i] + j] = (uint8_t)i;
+        }
+    for (int i = 0; i < r; ++i) {
+        if (pmask >> i & 1u) continue;
+        for (int l = 0; l < Q; ++l)
+            for (int x = 0; x < P; ++x) {
+                const int64_t t = L->off[i] + ((int64_t)l * p[i] - x - L->bmin[i]);
+                if (known[(int64_t)l * P + x]) w[t] ^= img[(int64_t)l * P + x];
+                else cnt[t] += 1;
+            }
+    }
+    int64_t tail = 0;
+    for (int i = 0; i < r; ++i) {
+        if (pmask >> i & 1u) continue;
+        for (int64_t j = 0; j < L->bins[i]; ++j)
+            if (cnt[L->off[i] + j] == 1) queue[tail++] = L->off[i] + j;
+    }
+    int64_t found = peel(P, Q, p, r, L, pmask, img, w, cnt, known, queue, tail, pid, unknown);
+    if (found < 0) return (int)found;
+    return found == unknown ? 0 : -ENOTRECOVERABLE;
 }
 
 /* ---- public entry points (stripes loop, optional threads) ---------------- */
@@ -201,11 +273,12 @@ struct job {
     const int *p;
     const struct layout *L;
     const uint64_t *in;
+    const uint64_t *data;   /* systematic decode: the data lines */
     uint64_t *out;
     const uint32_t *masks;
     int64_t nmasks;
     int64_t s0, s1;
-    int decode;
+    int decode;             /* 0 encode, 1 decode, 2 systematic decode */
     int status;
 };
 
@@ -231,13 +304,20 @@ static void *run_job(void *arg)
     } else {
         for (int64_t s = J->s0; s < J->s1; ++s) {
             uint32_t m = J->nmasks == 1 ? J->masks[0] : J->masks[s];
-            if (!oracle_katz(J->P, J->Q, J->p, J->n, m)) {
-                J->status = -ENOTRECOVERABLE;
-                break;
-            }
-            int r = decode_one(J->P, J->Q, J->p, J->n, J->L, m,
+            int r;
+            if (J->decode == 2) {
+                r = sys_decode_one(J->P, J->Q, J->p, J->n, J->L, m,
+                                   J->data + s * npix, J->in + s * total,
+                                   J->out + s * npix, w, cnt, known, queue, pid);
+            } else {
+                if (!oracle_katz(J->P, J->Q, J->p, J->n, m)) {
+                    J->status = -ENOTRECOVERABLE;
+                    break;
+                }
+                r = decode_one(J->P, J->Q, J->p, J->n, J->L, m,
                                J->in + s * total, J->out + s * npix, w, cnt,
                                known, queue, pid);
+            }
             if (r) { J->status = r; break; }
         }
     }
@@ -246,12 +326,13 @@ static void *run_job(void *arg)
 }
 
 static int run(int P, int Q, const int *p, int n, const uint64_t *in,
-               uint64_t *out, int64_t S, const uint32_t *masks, int64_t nmasks,
-               int decode, int nthreads)
+               const uint64_t *data, uint64_t *out, int64_t S,
+               const uint32_t *masks, int64_t nmasks, int decode, int nthreads)
 {
     int r = check_geometry(P, Q, p, n);
     if (r) return r;
     if (S < 0 || (S > 0 && (!in || !out))) return -EINVAL;
+    if (decode == 2 && (Q + n > 32 || (S > 0 && !data))) return -EINVAL;
     if (decode && (!masks || (nmasks != 1 && nmasks != S))) return -EINVAL;
     if (S == 0) return 0;
     struct layout L;
@@ -264,7 +345,8 @@ static int run(int P, int Q, const int *p, int n, const uint64_t *in,
     for (int t = 0; t < nthreads; ++t) {
         struct job *J = &jobs[t];
         J->P = P; J->Q = Q; J->n = n; J->p = p; J->L = &L;
-        J->in = in; J->out = out; J->masks = masks; J->nmasks = nmasks;
+        J->in = in; J->data = data; J->out = out;
+        J->masks = masks; J->nmasks = nmasks;
         J->s0 = S * t / nthreads; J->s1 = S * (t + 1) / nthreads;
         J->decode = decode;
     }
@@ -290,7 +372,7 @@ static int run(int P, int Q, const int *p, int n, const uint64_t *in,
 int oracle_encode(int P, int Q, const int *p, int n, const uint64_t *img,
                   uint64_t *proj, int64_t S, int nthreads)
 {
-    return run(P, Q, p, n, img, proj, S, NULL, 0, 0, nthreads);
+    return run(P, Q, p, n, img, NULL, proj, S, NULL, 0, 0, nthreads);
 }
 
 /* Decode S stripes proj[S][total_bins] into img[S][Q][P]. masks holds one
@@ -301,5 +383,17 @@ int oracle_decode(int P, int Q, const int *p, int n, const uint64_t *proj,
                   uint64_t *img, int64_t S, const uint32_t *masks,
                   int64_t nmasks, int nthreads)
 {
-    return run(P, Q, p, n, proj, img, S, masks, nmasks, 1, nthreads);
+    return run(P, Q, p, n, proj, NULL, img, S, masks, nmasks, 1, nthreads);
+}
+
+/* Systematic decode (see sys_decode_one) of S stripes: data[S][Q][P] holds
+ * the data lines (lost lines are never read), parity[S][total_bins] the r
+ * parity projections p[0..r-1]; img[S][Q][P] receives the whole image.
+ * Erasure mask bit l < Q: data line l lost; bit Q + i: projection i lost
+ * (Q + r <= 32). One mask for all stripes (nmasks == 1) or one per stripe. */
+int oracle_sys_decode(int P, int Q, const int *p, int r, const uint64_t *data,
+                      const uint64_t *parity, uint64_t *img, int64_t S,
+                      const uint32_t *masks, int64_t nmasks, int nthreads)
+{
+    return run(P, Q, p, r, parity, data, img, S, masks, nmasks, 2, nthreads);
 }

@@ -347,3 +347,159 @@ def test_erasure_masks():
     assert len(set(m.tolist())) > 400          # most of the C(12,4) = 495 patterns
     assert (inputs.erasure_masks(100, 6, 2, first=50) == inputs.erasure_masks(150, 6, 2)[50:]).all()
     assert len(inputs.all_masks(6, 2)) == 15 and len(inputs.all_masks(12, 4)) == 495
+
+
+# ------------------------------------------- systematic form (next to Sec. 2.3) --
+# The paper mentions a systematic Mojette code (Sec. 2.3, Sec. 4) without
+# defining it. Reading used here: the Q data lines are Q of the packets and
+# the r parity packets are Eq. 1 projections of the whole image; mask bit
+# l < Q marks data line l lost, bit Q + i parity projection i lost.
+
+SYS_CONFIGS = [
+    (128, 4, [-1, 1]),                 # 4 KB (6,4) systematic
+    (256, 4, [-1, 1]),                 # 8 KB (6,4)
+    (64, 8, [-2, -1, 1, 2]),           # 4 KB (12,8)
+    (128, 8, [-2, -1, 1, 2]),          # 8 KB (12,8)
+]
+
+
+def _sys_masks(Q, r):
+    """Every mask losing e data lines and f parity packets with e + f <= r."""
+    out = []
+    for m in range(1 << (Q + r)):
+        if bin(m).count("1") <= r:
+            out.append(m)
+    return out
+
+
+def _sys_incidence(P, Q, p, mask):
+    """GF(2) system of a systematic stripe over all Q*P pixels: one identity
+    row per pixel of a surviving data line (the packet is the line itself)
+    and the incidence rows of every surviving parity projection (Eq. 1)."""
+    r = len(p)
+    rows = []
+    for l in range(Q):
+        if not mask >> l & 1:
+            M = np.zeros((P, P * Q), dtype=np.uint8)
+            M[np.arange(P), l * P + np.arange(P)] = 1
+            rows.append(M)
+    surv = [i for i in range(r) if not mask >> (Q + i) & 1]
+    if surv:
+        rows.append(_incidence(P, Q, p, surv))
+    if not rows:
+        return np.zeros((0, P * Q), dtype=np.uint8), surv
+    return np.concatenate(rows, axis=0), surv
+
+
+def _sys_tiny_cases():
+    rng = np.random.default_rng(15040)
+    cases = []
+    for P in range(1, 7):
+        for Q in range(1, 5):
+            for _ in range(2):
+                r = int(rng.integers(1, 4))
+                p = sorted(rng.choice(np.arange(-4, 5), size=r, replace=False).tolist())
+                cases.append((P, Q, p))
+    return cases
+
+
+@pytest.mark.parametrize("P,Q,p", _sys_tiny_cases())
+def test_sys_decode_against_gf2_elimination(P, Q, p):
+    """Tiny images, every mask: whenever at least as many parity projections
+    survive as data lines are lost, the GF(2) system of the surviving
+    packets has full rank (any e distinct directions (p, 1) recover any e
+    lines: the e x e matrix [u^(p_i l_j)] is a generalised Vandermonde
+    matrix whose top monomial, matching sorted p to sorted l, occurs once,
+    so its determinant is nonzero) and the oracle returns the eliminated
+    solution, which is the image; a rank-deficient system is refused; and
+    an oracle success is always the unique solution."""
+    r = len(p)
+    img = _rand_img(1, Q, P, seed=P * 31 + Q)
+    par = oracle.encode(img, p)[0]
+    off, bins, _, _ = oracle.offsets(p, P, Q)
+    data = img.copy()
+    for mask in range(1 << (Q + r)):
+        lost = [l for l in range(Q) if mask >> l & 1]
+        A, surv = _sys_incidence(P, Q, p, mask)
+        rhs = np.concatenate([img[0, l] for l in range(Q) if l not in lost]
+                             + [par[off[i]:off[i] + bins[i]] for i in surv]) \
+            if A.shape[0] else np.zeros(0, np.uint64)
+        rank, sol = _gf2_solve(A, rhs) if A.shape[0] else (0, None)
+        garbage = data.copy()
+        garbage[0, lost] = np.uint64(0xDEADBEEF)         # lost lines are never read
+        try:
+            got = oracle.sys_decode(garbage, par[None], p, P, Q, mask)
+        except oracle.OracleError:
+            got = None
+        if len(surv) >= len(lost):
+            assert rank == P * Q, (mask, lost, surv)
+            assert (sol == img[0].ravel()).all()
+            assert got is not None and (got[0] == img[0]).all(), mask
+        if rank < P * Q:
+            assert got is None, mask
+        if got is not None:
+            assert rank == P * Q and (got[0] == img[0]).all(), mask
+
+
+@pytest.mark.parametrize("P,Q,p", SYS_CONFIGS)
+def test_sys_round_trip_every_mask(P, Q, p):
+    """Any e <= r lost data lines come back from any e surviving parity
+    projections, whatever else is lost; with no data line lost the decode is
+    the copy Sec. 4 expects of a systematic code."""
+    r = len(p)
+    img = _rand_img(2, Q, P, seed=P + 3 * Q)
+    par = oracle.encode(img, p)
+    masks = _sys_masks(Q, r)
+    if len(masks) > 120:                       # (12,8): a seeded sample
+        masks = [masks[i] for i in np.random.default_rng(8).choice(len(masks), 120, replace=False)]
+    for m in masks:
+        data = img.copy()
+        lost = [l for l in range(Q) if m >> l & 1]
+        data[:, lost] = np.uint64(0x0123456789ABCDEF)
+        assert (oracle.sys_decode(data, par, p, P, Q, m) == img).all(), m
+
+
+def test_sys_single_lost_line_closed_form():
+    """One lost line l0 under projection p: Eq. 1 read backwards, pixel
+    (l0, x) = bin l0 p - x XOR the other lines' pixels (l, x + (l - l0) p)
+    inside the image -- no peeling order involved."""
+    P, Q, p = 40, 5, [-2, 3]
+    img = _rand_img(1, Q, P, seed=11)[0]
+    par = oracle.encode(img[None], p)[0]
+    off, _, bmins, _ = oracle.offsets(p, P, Q)
+    for l0 in range(Q):
+        for i, pi in enumerate(p):
+            mask = (1 << l0) | (1 << (Q + 1 - i))    # the other projection lost too
+            expect = np.empty(P, np.uint64)
+            for x in range(P):
+                v = par[off[i] + l0 * pi - x - bmins[i]]
+                for l in range(Q):
+                    x2 = x + (l - l0) * pi
+                    if l != l0 and 0 <= x2 < P:
+                        v ^= img[l, x2]
+                expect[x] = v
+            got = oracle.sys_decode(img[None], par[None], p, P, Q, mask)[0]
+            assert (got[l0] == expect).all() and (expect == img[l0]).all()
+
+
+def test_sys_no_lost_line_is_a_copy():
+    """No data line lost: the output is the data, whatever the parity holds
+    (it is not read)."""
+    P, Q, p = 64, 4, [-1, 1]
+    img = _rand_img(3, Q, P, seed=5)
+    junk = np.full((3, oracle.total_bins(p, P, Q)), 0xFFFF, dtype=np.uint64)
+    for m in (0, 1 << Q, 3 << Q):
+        assert (oracle.sys_decode(img, junk, p, P, Q, m) == img).all()
+
+
+def test_sys_too_many_losses_refused():
+    """More lost lines than surviving parity with sum |p| < P: the GF(2)
+    system is rank deficient, so the oracle must refuse."""
+    P, Q, p = 32, 4, [-1, 1]
+    img = _rand_img(1, Q, P, seed=9)
+    par = oracle.encode(img, p)
+    for m in (0b0111, 0b0011 | 1 << Q, 0b1000 | 3 << Q):
+        A, _ = _sys_incidence(P, Q, p, m)
+        assert _gf2_solve(A, np.zeros(A.shape[0], np.uint64))[0] < P * Q
+        with pytest.raises(oracle.OracleError):
+            oracle.sys_decode(img, par, p, P, Q, m)
