@@ -19,6 +19,9 @@ The same line carries, unless switched off:
            same work as plain per-(geometry, mask) launches;
   served   the request server under closed-loop and Poisson load (p50/p99),
            against the same requests served one at a time;
+  systematic  the systematic form (data lines stored as they are, parity
+           projections): parity encode and in-place decode per number of
+           lost data lines, 8 KB stripes of (6,4) and (12,8);
   cpu_baseline  the oracle on the host cores, on a bounded sample.
 
 --impl reference times the CPU oracle (the slow plain implementation the
@@ -29,6 +32,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import itertools
 import json
 import os
 import statistics
@@ -350,6 +354,8 @@ def run_gpu(args, w):
         line["batched"] = run_batched(args, rank)
     if not args.no_served:
         line["served"] = run_served(args, rank)
+    if not args.no_systematic:
+        line["systematic"] = run_systematic(args, rank)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, masks, budget_s=args.cpu_seconds)
     if dist:
@@ -514,6 +520,93 @@ def run_batched(args, rank=0):
             "l2": "inputs larger than L2 (no flush)"}
 
 
+# --------------------------------------------------------- systematic arm --
+
+# The systematic form (the paper mentions it, Sec. 2.3 and Sec. 4, without a
+# definition): Q data lines stored as they are plus parity projections.
+SYSTEMATIC = dict(S=262144, codes=[("8KB(6,4)", 256, 4, [-1, 1]), ("8KB(12,8)", 128, 8, [-2, -1, 1, 2])],
+                  masks_per_e=6,
+                  desc="262144 stripes x 8 KB per code, systematic (6,4) = 4 data lines + 2 parity "
+                       "p={-1,1} and (12,8) = 8 data lines + 4 parity p={-2,-1,1,2}; parity encode, and "
+                       "in-place decode of e = 1..r lost data lines (up to 6 seeded lost-line sets per e, "
+                       "no parity lost)")
+
+
+def run_systematic(args, rank=0):
+    """Parity encode and in-place decode of the systematic form per number
+    of lost data lines e. Decode bytes per stripe (algorithmic, HBM): the
+    Q - e known lines and the e * P bins the path reads, plus the e * P
+    rebuilt pixels written = (Q + e) * P * 8. User-data GB/s counts the whole
+    Q * P * 8-byte block a read returns."""
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
+
+    S = SYSTEMATIC["S"]
+    peak, _ = measured_peaks()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 10))
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"workload": SYSTEMATIC["desc"], "l2": "inputs larger than L2 (no flush)", "codes": {}}
+    ok_all = True
+    launches = 0
+    for name, P, Q, p in SYSTEMATIC["codes"]:
+        plan = mj.Plan(P, Q, p, systematic=True)
+        seed = inputs.DEFAULT_SEED + 31 + 1000 * rank
+        ref = torch.from_numpy(inputs.stripes(S, Q, P, seed=seed).view(np.int64)).cuda()
+        data = ref.clone()
+        par = torch.empty((S, plan.total), dtype=torch.int64, device="cuda")
+        block = Q * P * 8
+        enc_ms = timed(lambda: mj.mojette_encode(plan, ref, par, S, stream))
+        launches += reps + 2
+        enc_bytes = S * (Q * P + plan.total) * 8
+        res = {"encode": {"ms": round(enc_ms, 4), "user_gbs": round(S * block / enc_ms / 1e6, 1),
+                          "hbm_gbs": round(enc_bytes / enc_ms / 1e6, 1),
+                          "frac": round(enc_bytes / enc_ms / 1e6 / peak, 4),
+                          "algorithmic_bytes_per_launch": enc_bytes},
+               "decode": {}}
+        rng = np.random.default_rng(seed)
+        for e in range(1, len(p) + 1):
+            sets = list(itertools.combinations(range(Q), e))
+            if len(sets) > SYSTEMATIC["masks_per_e"]:
+                sets = [sets[i] for i in sorted(rng.choice(len(sets), SYSTEMATIC["masks_per_e"], replace=False))]
+            ms_list = []
+            for lines in sets:
+                m = sum(1 << l for l in lines)
+                data[:, list(lines)] = 0x5A5A5A5A                   # lost: any contents
+                mj.mojette_sys_decode(plan, par, m, data, S, stream)
+                torch.cuda.synchronize()
+                ok_all &= bool(torch.equal(data, ref))
+                ms_list.append(timed(lambda: mj.mojette_sys_decode(plan, par, m, data, S, stream)))
+                launches += reps + 3
+            ms = statistics.median(ms_list)
+            dec_bytes = S * (Q + e) * P * 8
+            res["decode"][f"e={e}"] = {"ms": round(ms, 4), "user_gbs": round(S * block / ms / 1e6, 1),
+                                       "hbm_gbs": round(dec_bytes / ms / 1e6, 1),
+                                       "frac": round(dec_bytes / ms / 1e6 / peak, 4),
+                                       "algorithmic_bytes_per_launch": dec_bytes,
+                                       "lost_line_sets": len(sets),
+                                       "ms_min_max": [round(min(ms_list), 4), round(max(ms_list), 4)]}
+        res["decode"]["e=0"] = "no launch: the surviving data lines are the block"
+        out["codes"][name] = res
+        del ref, data, par
+        torch.cuda.empty_cache()
+    mj.mojette_device_status()
+    out["round_trip_ok"] = ok_all
+    out["gpu_launches"] = launches
+    return out
+
+
 # ------------------------------------------------------------- served arm --
 
 SERVED = dict(requests=3000, budget=16 << 30, slots=4, max_wave_stripes=65536,
@@ -626,6 +719,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the request-server measurement")
+    ap.add_argument("--no-systematic", action="store_true", help="skip the systematic-form measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=inputs.DEFAULT_SEED, help="seed of the stripe pixels")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="stripe slices of the e2e pipeline")

@@ -72,6 +72,8 @@ int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out);
 
 /* mojette_plan_ex flag: unused-bin removal. */
 #define MOJETTE_PLAN_TRIM_UNUSED 1u
+/* mojette_plan_ex flag: the systematic form of the code. */
+#define MOJETTE_PLAN_SYSTEMATIC 2u
 
 /*
  * mojette_plan_ex -- mojette_plan with options (flags 0: the same plan).
@@ -86,7 +88,19 @@ int mojette_plan(int P, int Q, const int *p, int n, mojette_plan_t *out);
  * with at least Q survivors. Building the plan builds the reconstruction
  * path of every such mask (host only; a fraction of a second at n = 12);
  * it requires n <= 20.
- * Errors: as mojette_plan, -EINVAL for unknown flags or n > 20.
+ * MOJETTE_PLAN_SYSTEMATIC: the systematic form of the code, which the paper
+ * mentions (Sec. 2.3: "a systematic version ... is currently under
+ * development"; Sec. 4: such a code decodes a 0-erasure read by a copy)
+ * without defining it. Here the Q data lines are themselves Q of the
+ * packets and the n projections p[0..n-1] are the parity packets, each the
+ * projection of the whole image (Eq. 1, encoded by mojette_encode as
+ * usual). Erasure masks of such a plan have Q + n bits: bit l < Q marks data
+ * line l lost, bit Q + i marks projection i lost; any e lost data lines come
+ * back from any e surviving projections (mojette_sys_decode). Requires
+ * Q + n <= 32; cannot be combined with MOJETTE_PLAN_TRIM_UNUSED.
+ * Errors: as mojette_plan, -EINVAL for unknown flags, n > 20 with
+ * MOJETTE_PLAN_TRIM_UNUSED, or Q + n > 32 (or both flags) with
+ * MOJETTE_PLAN_SYSTEMATIC.
  */
 int mojette_plan_ex(int P, int Q, const int *p, int n, uint32_t flags,
                     mojette_plan_t *out);
@@ -154,12 +168,41 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
  * 28000 words, e.g. 16 KB-wide lines at Q = 4); larger stripes get -EINVAL
  * before any launch (cut objects into smaller stripes). The reconstruction path for
  * the surviving set is computed on the host on first use and cached in the
- * plan (the paper's pre-determined path, Sec. 2.2 and Sec. 3.1).
+ * plan (the paper's pre-determined path, Sec. 2.2 and Sec. 3.1). A
+ * systematic plan decodes with mojette_sys_decode instead (-EINVAL here).
  * Errors: -EINVAL, -ERANGE, -ENOTRECOVERABLE, -ENOMEM, -EIO.
  */
 int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
                    uint32_t erasure_mask, uint64_t *d_img, int64_t S,
                    mojette_stream_t stream);
+
+/*
+ * mojette_sys_decode -- rebuild, in place, the lost data lines of S stripes
+ * of a systematic plan (MOJETTE_PLAN_SYSTEMATIC) that all lost the same
+ * packets. The paper leaves the systematic form undefined (Sec. 2.3,
+ * Sec. 4); the decode here removes (XOR) the known lines' pixels from the
+ * surviving projections' bins -- Eq. 1's sum split into known and lost
+ * pixels -- and runs the inverse of Sec. 2.2 on the lost lines only, one
+ * surviving projection dedicated to each.
+ *   d_parity      [S][total] uint64 bins of the n parity projections, read;
+ *                 the slices of lost projections are never read;
+ *   erasure_mask  bit l < Q: data line l lost; bit Q + i: projection i lost;
+ *   d_data        [S][Q][P] uint64 pixels: the surviving data lines are
+ *                 read, the lost ones (any contents) are overwritten with
+ *                 their values; no other word is written.
+ * With no data line lost nothing is launched (the data is already whole:
+ * the copy Sec. 4 expects of a systematic code). At most 8 data lines may
+ * be lost per call (-EINVAL beyond), and at least as many projections must
+ * survive as lines are lost, else -ENOTRECOVERABLE. The lost lines' bins
+ * plus zero columns must fit in one CTA's shared memory (as for
+ * mojette_decode), else -EINVAL. The path for the mask is computed on the
+ * host on first use and cached in the plan.
+ * Errors: -EINVAL (not a systematic plan, mask bits beyond Q + n, ...),
+ * -ERANGE, -ENOTRECOVERABLE, -ENOMEM, -EIO.
+ */
+int mojette_sys_decode(mojette_plan_t plan, const uint64_t *d_parity,
+                       uint32_t erasure_mask, uint64_t *d_data, int64_t S,
+                       mojette_stream_t stream);
 
 /*
  * mojette_decode_noalloc -- mojette_decode for callers that must not allocate
@@ -173,6 +216,7 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
  * every GPU loading the library holds until the process exits; schedules of
  * more than 16384 steps are refused with -ENOSPC. The caller still passes the
  * inputs and outputs, as for mojette_decode.
+ * Systematic plans are refused (-EINVAL).
  * Every call shares that scratch and overwrites it (on `stream`, before the
  * kernel): calls that can overlap on the GPU -- on different streams without
  * ordering between them -- race and may decode with another call's path.
@@ -204,6 +248,10 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
  *                 l+1 of the same front rebuilds in the same step (fronts
  *                 visit their lines from Q-1 down to 0 within a step);
  *   n_steps       receives the number of steps.
+ * For a systematic plan the path rebuilds only the lost data lines: the
+ * arrays get one entry per lost line, in increasing line order, line l of
+ * the step and forward words being the l-th lost line (no entry and no
+ * step when no line is lost; no step when one is).
  * Any output pointer may be NULL. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
  */
 int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask,
@@ -233,6 +281,9 @@ typedef struct mojette_stripe {
     uint64_t *dst;           /* device, 8-byte aligned: encode writes the
                                 [total] bins, decode the [Q][P] pixels */
 } mojette_stripe_t;
+/* A decode stripe of a systematic plan is mojette_sys_decode's: src the
+ * parity bins, dst the data lines, rebuilt in place; the mask has Q + n
+ * bits. Such stripes with no data line lost launch nothing. */
 
 /* Opaque batch: the stripes' device tables, side streams, an optional CUDA
  * graph. Not thread-safe: one host thread at a time per batch. */
@@ -300,10 +351,13 @@ int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps)
 
 /*
  * mojette_batch_info -- the batch's shape (any pointer may be NULL):
- *   launches    kernel launches per run (one per (operation, plan));
+ *   launches    kernel launches per run (one per (operation, plan), and
+ *               for a systematic plan's decodes one per count of lost data
+ *               lines, none for those that lost none);
  *   groups      (plan, mask) groups of the decode stripes;
  *   work_items  decode work items (one warp's stripes each);
- *   configs     6 words per launch: op, Q, P, then for decode the kernel
+ *   configs     6 words per launch: op, Q (decode: lines rebuilt per
+ *               stripe, a systematic launch's lost lines), P, then for decode the kernel
  *               (0 decode_lines, 1 decode_fronts, 2 decode_stream,
  *               3 decode_cols), work
  *               items per CTA and
@@ -373,7 +427,9 @@ int mojette_server_create(int64_t device_budget_bytes, int slots,
  * buffers fit the pool; a request that does not fit waits (later requests
  * wait behind it). A wave's requests whose host buffers follow each other
  * exactly (and whose device buffers do too) are copied in one transfer.
- * Errors (nothing is queued): -EINVAL, -ENOTRECOVERABLE (a read's mask
+ * Errors (nothing is queued): -EINVAL (also a read of a systematic plan:
+ * its decode takes data and parity in place, see mojette_sys_decode and
+ * the batch calls), -ENOTRECOVERABLE (a read's mask
  * leaves fewer than Q projections), -ENOSPC (a request whose input or
  * output exceeds half the budget, or larger than max_wave_stripes), or an
  * error of a wave launched meanwhile (see mojette_server_poll).

@@ -55,6 +55,7 @@ def lib():
             L.mojette_encode.argtypes = [_PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
+            L.mojette_sys_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_batch_create.argtypes = [_PTR, _I64, _U32, ctypes.POINTER(_PTR)]
             L.mojette_batch_update.argtypes = [_PTR, _PTR, _I64, _PTR]
@@ -76,7 +77,7 @@ def lib():
             for name in ("mojette_plan", "mojette_plan_ex", "mojette_plan_bins", "mojette_plan_config",
                          "mojette_plan_destroy",
                          "mojette_plan_info",
-                         "mojette_encode", "mojette_decode", "mojette_decode_noalloc",
+                         "mojette_encode", "mojette_decode", "mojette_decode_noalloc", "mojette_sys_decode",
                          "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
                          "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
                          "mojette_batch_destroy", "mojette_server_create", "mojette_server_submit",
@@ -132,19 +133,23 @@ def _stream(stream) -> int:
 
 
 MOJETTE_PLAN_TRIM_UNUSED = 1
+MOJETTE_PLAN_SYSTEMATIC = 2
 
 
 class Plan:
     """Owns a ``mojette_plan_t``; geometry (P, Q, p) and its bin layout.
     ``trim=True``: unused-bin removal (mojette_plan_ex); ``full_bin`` then
     maps each stored word of a stripe's block to its bin in the full
-    projection (mojette_plan_bins)."""
+    projection (mojette_plan_bins). ``systematic=True``: the systematic form
+    (the Q data lines are packets, ``p`` the parity projections; decode with
+    mojette_sys_decode)."""
 
-    def __init__(self, P: int, Q: int, p, trim: bool = False):
+    def __init__(self, P: int, Q: int, p, trim: bool = False, systematic: bool = False):
         self.P, self.Q, self.p = int(P), int(Q), [int(v) for v in p]
+        self.systematic = bool(systematic)
         arr = (ctypes.c_int * len(self.p))(*self.p)
         h = _PTR()
-        flags = MOJETTE_PLAN_TRIM_UNUSED if trim else 0
+        flags = (MOJETTE_PLAN_TRIM_UNUSED if trim else 0) | (MOJETTE_PLAN_SYSTEMATIC if systematic else 0)
         _check(lib().mojette_plan_ex(self.P, self.Q, arr, len(self.p), flags, ctypes.byref(h)),
                "mojette_plan_ex")
         self.handle = h.value
@@ -175,7 +180,8 @@ def mojette_plan(P: int, Q: int, p) -> Plan:
 
 
 def mojette_plan_ex(P: int, Q: int, p, flags: int = 0) -> Plan:
-    return Plan(P, Q, p, trim=bool(flags & MOJETTE_PLAN_TRIM_UNUSED))
+    return Plan(P, Q, p, trim=bool(flags & MOJETTE_PLAN_TRIM_UNUSED),
+                systematic=bool(flags & MOJETTE_PLAN_SYSTEMATIC))
 
 
 def mojette_plan_destroy(plan: Plan) -> None:
@@ -201,7 +207,8 @@ def mojette_plan_config(plan: Plan, config: dict | None = None) -> dict:
 
 
 def geometry_key(plan: Plan) -> str:
-    return f"P{plan.P}-Q{plan.Q}-p{','.join(str(v) for v in plan.p)}" + ("-trimmed" if plan.trimmed else "")
+    return (f"P{plan.P}-Q{plan.Q}-p{','.join(str(v) for v in plan.p)}" + ("-trimmed" if plan.trimmed else "")
+            + ("-systematic" if plan.systematic else ""))
 
 
 def save_tuning(plans, path: str) -> None:
@@ -260,6 +267,17 @@ def mojette_decode(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None =
                                 _addr(d_img), int(S), _stream(stream)), "mojette_decode")
 
 
+def mojette_sys_decode(plan: Plan, d_parity, erasure_mask: int, d_data, S: int | None = None,
+                       stream=None) -> None:
+    """Systematic plan: rebuild in place the data lines of d_data [S][Q][P]
+    that erasure_mask marks lost (bits 0..Q-1; bits Q.. mark lost parity
+    projections of d_parity [S][total])."""
+    if S is None:
+        S = d_data.numel() // (plan.P * plan.Q)
+    _check(lib().mojette_sys_decode(plan.handle, _addr(d_parity), int(erasure_mask) & 0xFFFFFFFF,
+                                    _addr(d_data), int(S), _stream(stream)), "mojette_sys_decode")
+
+
 def mojette_decode_noalloc(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None = None,
                            stream=None) -> None:
     """mojette_decode without any device allocation (fixed in-library scratch;
@@ -285,8 +303,11 @@ def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:
     forward = (ctypes.c_uint32 * max(T, 1))()
     _check(lib().mojette_schedule(plan.handle, int(erasure_mask) & 0xFFFFFFFF, left, right, split,
                                   steps, forward, T, ctypes.byref(nsteps)), "mojette_schedule")
-    return {"left": list(left), "right": list(right), "split": list(split),
-            "steps": list(steps)[:T], "forward": list(forward)[:T], "T": T}
+    lines = Q
+    if plan.systematic:   # one entry per lost data line
+        lines = bin(int(erasure_mask) & ((1 << Q) - 1)).count("1")
+    return {"left": list(left)[:lines], "right": list(right)[:lines], "split": list(split)[:lines],
+            "steps": list(steps)[:T], "forward": list(forward)[:T], "T": T, "lines": lines}
 
 
 # ---- batches -----------------------------------------------------------------

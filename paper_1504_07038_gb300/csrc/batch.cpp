@@ -34,6 +34,9 @@ struct Klass {
     int64_t wbase = 0, wcap = 0;    // its region of the work table
     int64_t nwork = 0;              // work items in use
     int maxp = 0, maxT = 0;
+    int lines = 0;                  // lines rebuilt per stripe (systematic: lost lines)
+    int span = 0;                   // widest row distance between two of them
+    bool sys = false;               // systematic plan: in-place decode of the lost lines
     int32_t rowoff[kMaxLines] = {};   // row phases of its largest group
     DecodeConfig dcfg;
     EncodeConfig ecfg;
@@ -105,7 +108,17 @@ int fill_work(Batch &b, Klass &k, int G)
 
 int class_layout(const Klass &k, const DecodeConfig &cfg, DecodeLayout *L)
 {
-    return decode_layout(k.plan->P, k.plan->Q, k.maxp, k.maxT, cfg, k.rowoff, L);
+    if (k.sys && cfg.kernel != 0) return -EINVAL;   // decode_lines only
+    return decode_layout(k.plan->P, k.lines, k.span, k.maxp, k.maxT, cfg, k.rowoff, L);
+}
+
+// Lost data lines of a systematic decode stripe (0 otherwise).
+int sys_lines(const mojette_stripe_t &d)
+{
+    const Plan *pl = reinterpret_cast<const Plan *>(d.plan);
+    if (d.op != MOJETTE_OP_DECODE || !pl->systematic) return 0;
+    const uint32_t data = pl->Q >= 32 ? 0xFFFFFFFFu : (1u << pl->Q) - 1u;
+    return __builtin_popcount(d.erasure_mask & data);
 }
 
 int launch_class(Batch &b, const Klass &k, cudaStream_t st)
@@ -134,7 +147,10 @@ int launch_class(Batch &b, const Klass &k, cudaStream_t st)
     }
     DecBatchArgs a{};
     a.P = k.plan->P;
-    a.Q = k.plan->Q;
+    a.Q = k.lines;
+    a.sys = k.sys;
+    a.Qd = k.plan->Q;
+    a.span = k.span;
     a.maxp = k.maxp;
     a.maxT = k.maxT;
     for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = k.rowoff[l];
@@ -169,6 +185,7 @@ int ensure_streams(Batch &b, size_t n)
 int launch_all(Batch &b, cudaStream_t st)
 {
     int err = 0;
+    if (b.classes.empty()) return 0;
     if (b.classes.size() == 1) return launch_class(b, b.classes[0], st);
     if ((err = ensure_streams(b, b.classes.size()))) return err;
     if ((err = record_cuda(cudaEventRecord(b.fork, st)))) return err;
@@ -228,15 +245,17 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         if (d.op == MOJETTE_OP_ENCODE && pl->P % 2 == 0 && !aligned16(d.src)) return -ERANGE;
         if (d.op == MOJETTE_OP_DECODE) {
             if (pl->Q > kMaxLines) return -EINVAL;
-            if (pl->n < 32 && (d.erasure_mask >> pl->n)) return -EINVAL;
+            const int bits = pl->systematic ? pl->Q + pl->n : pl->n;
+            if (bits < 32 && (d.erasure_mask >> bits)) return -EINVAL;
         }
     }
-    // order by (op, plan, mask)
+    // order by (op, plan, lost data lines of a systematic decode, mask)
     std::vector<int64_t> idx(count);
     std::iota(idx.begin(), idx.end(), 0);
     auto key = [&](int64_t i) {
         const mojette_stripe_t &d = stripes[i];
-        return std::make_tuple(d.op, (uintptr_t)d.plan, d.op == MOJETTE_OP_DECODE ? d.erasure_mask : 0u);
+        return std::make_tuple(d.op, (uintptr_t)d.plan, sys_lines(d),
+                               d.op == MOJETTE_OP_DECODE ? d.erasure_mask : 0u);
     };
     std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return key(x) < key(y); });
 
@@ -248,13 +267,24 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         k.op = d0.op;
         k.plan = reinterpret_cast<Plan *>(d0.plan);
         k.first = r;
+        const int kl = sys_lines(d0);
         int64_t e = r;
-        while (e < count && stripes[idx[e]].op == k.op && stripes[idx[e]].plan == d0.plan) ++e;
+        while (e < count && stripes[idx[e]].op == k.op && stripes[idx[e]].plan == d0.plan &&
+               sys_lines(stripes[idx[e]]) == kl)
+            ++e;
         k.count = e - r;
+        k.sys = k.op == MOJETTE_OP_DECODE && k.plan->systematic;
+        if (k.sys && kl == 0) {
+            // systematic reads that lost no data line: the data is whole, no launch
+            r = e;
+            continue;
+        }
         if (k.op == MOJETTE_OP_ENCODE) {
             k.ecfg = k.plan->tuned_enc ? k.plan->enc_cfg : EncodeConfig();
         } else {
             k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : DecodeConfig();
+            if (k.sys && k.dcfg.kernel != 0) k.dcfg = DecodeConfig();
+            k.lines = k.sys ? kl : k.plan->Q;
             k.gbase = (int64_t)groups.size();
             int64_t big = 0;
             Schedule *big_sc = nullptr;
@@ -271,7 +301,10 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 gr.steps = dsteps;
                 gr.T = sc->T;
                 gr.fwd = sc->fwd;
-                for (int l = 0; l < k.plan->Q; ++l) {
+                gr.known = sc->known;
+                for (int l = 0; l < sc->lines; ++l) gr.lpos[l] = sc->lpos[l];
+                k.span = std::max(k.span, sc->lines > 0 ? sc->lpos[sc->lines - 1] - sc->lpos[0] : 0);
+                for (int l = 0; l < sc->lines; ++l) {
                     gr.p[2 * l] = sc->pL[l];
                     gr.p[2 * l + 1] = sc->pR[l];
                     gr.src[2 * l] = (int32_t)sc->srcL[l];
@@ -364,9 +397,11 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             DecodeLayout L;
             if ((err = class_layout(k, k.dcfg, &L))) {
                 // a tuned configuration that no longer fits: the defaults,
-                // else decode_fronts (G down to one stripe)
+                // else decode_fronts (G down to one stripe; not for the
+                // systematic form)
                 k.dcfg = DecodeConfig();
                 if ((err = class_layout(k, k.dcfg, &L))) {
+                    if (k.sys) return err;
                     k.dcfg.kernel = 1;
                     if ((err = class_layout(k, k.dcfg, &L))) return err;
                 }
@@ -453,14 +488,19 @@ int tune(Batch &b, cudaStream_t st, int reps)
         } else {
             struct Cand { int kernel, gpc, persist, rowoff; };
             std::vector<Cand> cands;
-            if (k.plan->Q <= 8) {
+            if (k.sys) {
+                for (int sp : {0, 1})
+                    for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});
+                cands.push_back({0, 4, 1, 1});
+            } else if (k.plan->Q <= 8) {
                 for (int sp : {0, 1})
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});
                 for (int kern : {2, 3})
                     for (int g : {1, 2, 4, 8}) cands.push_back({kern, g, 0, 0});
                 for (int kern : {0, 3}) cands.push_back({kern, 4, 1, 1});
             }
-            for (int g : {1, 2, 4}) cands.push_back({1, g, 0, 0});
+            if (!k.sys)
+                for (int g : {1, 2, 4}) cands.push_back({1, g, 0, 0});
             float best = 1e30f;
             DecodeConfig best_cfg = k.dcfg;
             for (const Cand &c : cands) {
@@ -599,7 +639,7 @@ int mojette_batch_info(mojette_batch_t batch, int64_t *launches, int64_t *groups
             const Klass &k = b->classes[i];
             int32_t *c = configs + 6 * i;
             c[0] = k.op;
-            c[1] = k.plan->Q;
+            c[1] = k.op == MOJETTE_OP_DECODE ? k.lines : k.plan->Q;
             c[2] = k.plan->P;
             c[3] = k.op == MOJETTE_OP_DECODE ? k.dcfg.kernel : 0;
             c[4] = k.op == MOJETTE_OP_DECODE ? k.dcfg.gpc : k.ecfg.tile_bytes;

@@ -40,6 +40,42 @@ uint32_t *device_status_ptr(int *err)
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Decode arguments of one schedule (everything but the buffers, steps and status).
+static void fill_decode_args(const Plan &pl, const Schedule &sc, int64_t S, DecodeArgs *a)
+{
+    std::memset(a, 0, sizeof(*a));
+    a->S = S;
+    a->total = pl.total;
+    a->P = pl.P;
+    a->Q = sc.lines;
+    a->sys = pl.systematic;
+    a->Qd = pl.Q;
+    a->known = sc.known;
+    a->T = sc.T;
+    a->fwd = sc.fwd;
+    for (int l = 0; l < sc.lines; ++l) {
+        a->lpos[l] = sc.lpos[l];
+        a->pL[l] = sc.pL[l];
+        a->pR[l] = sc.pR[l];
+        a->split[l] = sc.split[l];
+        a->srcL[l] = sc.srcL[l];
+        a->srcR[l] = sc.srcR[l];
+    }
+    a->chunk_w = sc.chunk_w;
+    for (int c = 0; c < kStreamChunks; ++c) {
+        a->chunk_wait[c] = sc.chunk_wait[c];
+        a->chunk_done[c] = sc.chunk_done[c];
+    }
+}
+
+// Erasure mask bits a plan defines: n projections, or for a systematic plan
+// Q data lines then n projections.
+static bool mask_in_range(const Plan &pl, uint32_t mask)
+{
+    const int bits = pl.systematic ? pl.Q + pl.n : pl.n;
+    return bits >= 32 || (mask >> bits) == 0;
+}
+
 }  // namespace mojette
 
 using namespace mojette;
@@ -85,9 +121,14 @@ int mojette_plan_ex(int P, int Q, const int *p, int n, uint32_t flags, mojette_p
 {
     if (!out) return -EINVAL;
     *out = nullptr;
-    if (flags & ~(uint32_t)MOJETTE_PLAN_TRIM_UNUSED) return -EINVAL;
+    if (flags & ~(uint32_t)(MOJETTE_PLAN_TRIM_UNUSED | MOJETTE_PLAN_SYSTEMATIC)) return -EINVAL;
+    if (flags & MOJETTE_PLAN_SYSTEMATIC) {
+        // mask bits: Q data lines then n parity projections
+        if ((flags & MOJETTE_PLAN_TRIM_UNUSED) || Q < 1 || n < 1 || Q + n > 32) return -EINVAL;
+    }
     int err = mojette_plan(P, Q, p, n, out);
     if (err) return err;
+    if (flags & MOJETTE_PLAN_SYSTEMATIC) reinterpret_cast<Plan *>(*out)->systematic = true;
     if (flags & MOJETTE_PLAN_TRIM_UNUSED) {
         if ((err = trim_unused_bins(*reinterpret_cast<Plan *>(*out)))) {
             mojette_plan_destroy(*out);
@@ -208,8 +249,8 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
 {
     if (!plan || S < 0) return -EINVAL;
     Plan *pl = reinterpret_cast<Plan *>(plan);
-    if (pl->Q > kMaxLines) return -EINVAL;
-    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;   // bits beyond n
+    if (pl->Q > kMaxLines || pl->systematic) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;   // bits beyond n
     int err = 0;
     Schedule *sc = get_schedule(*pl, erasure_mask, &err);
     if (!sc) return err;
@@ -219,29 +260,39 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     uint32_t *dsteps = nullptr;
     if ((err = schedule_on_device(*pl, *sc, &dsteps))) return err;
     DecodeArgs a;
+    fill_decode_args(*pl, *sc, S, &a);
     a.proj = d_proj;
     a.img = d_img;
-    a.S = S;
-    a.total = pl->total;
-    a.P = pl->P;
-    a.Q = pl->Q;
-    a.T = sc->T;
     a.steps = dsteps;
-    a.fwd = sc->fwd;
-    for (int l = 0; l < pl->Q; ++l) {
-        a.pL[l] = sc->pL[l];
-        a.pR[l] = sc->pR[l];
-        a.split[l] = sc->split[l];
-        a.srcL[l] = sc->srcL[l];
-        a.srcR[l] = sc->srcR[l];
-    }
     const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
     for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
-    a.chunk_w = sc->chunk_w;
-    for (int c = 0; c < kStreamChunks; ++c) {
-        a.chunk_wait[c] = sc->chunk_wait[c];
-        a.chunk_done[c] = sc->chunk_done[c];
-    }
+    a.status = device_status_ptr(&err);
+    if (err) return err;
+    return launch_decode(a, (cudaStream_t)stream);
+}
+
+int mojette_sys_decode(mojette_plan_t plan, const uint64_t *d_parity, uint32_t erasure_mask,
+                       uint64_t *d_data, int64_t S, mojette_stream_t stream)
+{
+    if (!plan || S < 0) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (!pl->systematic || pl->Q > kMaxLines) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    if (S == 0 || sc->lines == 0) return 0;     // no data line lost: nothing to do
+    if (!d_data || !d_parity) return -EINVAL;
+    if (!aligned16(d_data) || !aligned16(d_parity)) return -ERANGE;
+    uint32_t *dsteps = nullptr;
+    if ((err = schedule_on_device(*pl, *sc, &dsteps))) return err;
+    DecodeArgs a;
+    fill_decode_args(*pl, *sc, S, &a);
+    a.proj = d_parity;
+    a.img = d_data;
+    a.steps = dsteps;
+    const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
@@ -252,8 +303,8 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
 {
     if (!plan || S < 0) return -EINVAL;
     Plan *pl = reinterpret_cast<Plan *>(plan);
-    if (pl->Q > kMaxLines) return -EINVAL;
-    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;
+    if (pl->Q > kMaxLines || pl->systematic) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
     int err = 0;
     Schedule *sc = get_schedule(*pl, erasure_mask, &err);   // host memory only
     if (!sc) return err;
@@ -264,29 +315,12 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
     uint32_t *dsteps = nullptr;
     if ((err = noalloc_schedule_copy(*sc, (cudaStream_t)stream, &dsteps))) return err;
     DecodeArgs a;
+    fill_decode_args(*pl, *sc, S, &a);
     a.proj = d_proj;
     a.img = d_img;
-    a.S = S;
-    a.total = pl->total;
-    a.P = pl->P;
-    a.Q = pl->Q;
-    a.T = sc->T;
     a.steps = dsteps;
-    a.fwd = sc->fwd;
-    for (int l = 0; l < pl->Q; ++l) {
-        a.pL[l] = sc->pL[l];
-        a.pR[l] = sc->pR[l];
-        a.split[l] = sc->split[l];
-        a.srcL[l] = sc->srcL[l];
-        a.srcR[l] = sc->srcR[l];
-    }
     const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
     for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
-    a.chunk_w = sc->chunk_w;
-    for (int c = 0; c < kStreamChunks; ++c) {
-        a.chunk_wait[c] = sc->chunk_wait[c];
-        a.chunk_done[c] = sc->chunk_done[c];
-    }
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
@@ -299,11 +333,11 @@ int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *surviv
     if (!plan) return -EINVAL;
     Plan *pl = reinterpret_cast<Plan *>(plan);
     if (pl->Q > kMaxLines) return -EINVAL;
-    if (pl->n < 32 && (erasure_mask >> pl->n)) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
     int err = 0;
     Schedule *sc = get_schedule(*pl, erasure_mask, &err);
     if (!sc) return err;
-    for (int l = 0; l < pl->Q; ++l) {
+    for (int l = 0; l < sc->lines; ++l) {
         if (survivors) survivors[l] = sc->projL[l];
         if (survivors2) survivors2[l] = sc->projR[l];
         if (split) split[l] = sc->split[l];

@@ -14,8 +14,8 @@ int decode_bank_slots(int Q)
     return (16 % G == 0 && G < 16) ? 16 / G : 1;
 }
 
-int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, const int32_t *rowoff,
-                  DecodeLayout *L)
+int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig &cfg,
+                  const int32_t *rowoff, DecodeLayout *L)
 {
     int err = 0, dev = 0, cap = 0, cap_sm = 0;
     if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
@@ -24,9 +24,9 @@ int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, con
     if ((err = record_cuda(cudaDeviceGetAttribute(&cap_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev))))
         return err;
     // Zero columns between rows: one more than the widest offset (l2 - l) p
-    // of a bin line, so that a front one step past its last pixel still
-    // reads inside the stripe.
-    L->reach = (Q - 1) * maxp + 1;
+    // of a bin line (rows `span` apart at most), so that a front one step
+    // past its last pixel still reads inside the stripe.
+    L->reach = span * maxp + 1;
     L->RP = P + L->reach;
     L->TS = (maxT + 3) / 4 * 4 + 4;
     for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = L->reach + l * L->RP;
@@ -114,6 +114,9 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     a.total = d.total;
     a.P = d.P;
     a.Q = d.Q;
+    a.Qd = d.Qd;
+    a.grp.known = d.known;
+    for (int l = 0; l < kMaxLines; ++l) a.grp.lpos[l] = d.lpos[l];
     a.grp.steps = d.steps;
     a.grp.T = d.T;
     a.grp.fwd = d.fwd;
@@ -143,12 +146,24 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
     if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;
     DecodeLayout L;
-    int err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
+    if (d.sys) {
+        // the systematic form: residual bins into the lost rows, then the
+        // path on them (decode_lines only; none needed for one lost line)
+        cfg.kernel = 0;
+        const int span = d.lpos[d.Q - 1] - d.lpos[0];
+        int err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
+        if (err) return err;
+        const int64_t nitems = (d.S + L.G - 1) / L.G;
+        if ((err = launch_sys_residual<false>(a, L, nitems, st))) return err;
+        if (d.T == 0) return 0;
+        return launch_decode_kernel<false>(a, L, cfg, nitems, st, true);
+    }
+    int err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
     if (err == -EINVAL && cfg.kernel != 1) {
         // a warp's G stripes do not fit in shared memory: decode_fronts sizes
         // G to what fits, down to one stripe
         cfg.kernel = 1;
-        err = decode_layout(d.P, d.Q, maxp, d.T, cfg, d.rowoff, &L);
+        err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
     }
     if (err) return err;
     return launch_decode_kernel<false>(a, L, cfg, (d.S + L.G - 1) / L.G, st);

@@ -8,7 +8,8 @@ namespace mojette {
 int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaStream_t st)
 {
     DecodeLayout L;
-    int err = decode_layout(b.P, b.Q, b.maxp, b.maxT, cfg, b.rowoff, &L);
+    if (b.sys && cfg.kernel != 0) return -EINVAL;
+    int err = decode_layout(b.P, b.Q, b.span, b.maxp, b.maxT, cfg, b.rowoff, &L);
     if (err) return err;
     DecParams a;
     std::memset(&a, 0, sizeof(a));
@@ -19,7 +20,13 @@ int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaSt
     a.dstp = b.dstp;
     a.P = b.P;
     a.Q = b.Q;
-    return launch_decode_kernel<true>(a, L, cfg, b.nwork, st);
+    a.Qd = b.Qd;
+    if (b.sys) {
+        // residual bins into the lost rows, then the path (none for one lost line)
+        if ((err = launch_sys_residual<true>(a, L, b.nwork, st))) return err;
+        if (b.maxT == 0) return 0;
+    }
+    return launch_decode_kernel<true>(a, L, cfg, b.nwork, st, b.sys);
 }
 
 }  // namespace mojette

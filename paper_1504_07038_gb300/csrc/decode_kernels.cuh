@@ -59,7 +59,8 @@ struct DecParams {
     uint64_t *const *dstp;
     // layout (both forms)
     int64_t total;
-    int P, Q;
+    int P, Q;     // Q: lines rebuilt (a systematic decode: the lost data lines)
+    int Qd;       // systematic: data lines per stripe (img stripe pitch Qd * P)
     int reach;    // zero columns before, between and after the rows of a stripe
     int RP;       // row pitch in columns: P + reach (+ room for row phases)
     int SWc;      // columns per stripe slot
@@ -332,7 +333,13 @@ __global__ void __launch_bounds__(32) decode_fronts(const __grid_constant__ DecP
 // within a front; the chain values are a segmented suffix XOR over the lines,
 // done with log2(Q) rounds of warp shuffles, so every lane of every line
 // works at every step and a step costs one shared-memory round trip.
-template <int QT, bool BATCHED>
+//
+// SYS: the systematic form. The lines rebuilt are the lost data lines (Q of
+// them, at image rows lpos[]) of the data buffer (img, or dstp[s] batched, Qd
+// lines per stripe), which sys_residual has already filled with their
+// residual bins (the known lines removed); the rows are staged from there
+// and the rebuilt lines written back in place.
+template <int QT, bool BATCHED, bool SYS = false>
 __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecParams a)
 {
     extern __shared__ __align__(16) uint64_t sm[];
@@ -382,7 +389,10 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         }
         // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
         const int p = gr.p[ls];
-        auto off = [&](int l2) { return (a.rowbase[l2] - myrow + (l2 - l) * p) * G * 8; };
+        auto off = [&](int l2) {
+            const int dl = SYS ? gr.lpos[l2] - gr.lpos[l] : l2 - l;
+            return (a.rowbase[l2] - myrow + dl * p) * G * 8;
+        };
         d0 = off(has_next ? l + 1 : 0);
 #pragma unroll
         for (int k = 1; k < Q - 1; ++k) dk[k - 1] = off((l + 1 + k) % Q);
@@ -439,13 +449,23 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         }
 
         if (copy_ok && gg < nst) {
-            const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
-            for (int ll = 0; ll < Q; ++ll) {
-                const int sp = grp().split[ll];
-                const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
-                uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
-                for (int x = xk; x < P; x += XK)
-                    cp_async8(dst + x * G, src + ((x < sp ? sl : sr) - x));
+            if constexpr (SYS) {
+                // the residual bins, in pixel order, in the lost rows
+                const uint64_t *dat = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
+                for (int ll = 0; ll < Q; ++ll) {
+                    const uint64_t *srow = dat + (int64_t)grp().lpos[ll] * P;
+                    uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
+                    for (int x = xk; x < P; x += XK) cp_async8(dst + x * G, srow + x);
+                }
+            } else {
+                const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+                for (int ll = 0; ll < Q; ++ll) {
+                    const int sp = grp().split[ll];
+                    const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
+                    uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
+                    for (int x = xk; x < P; x += XK)
+                        cp_async8(dst + x * G, src + ((x < sp ? sl : sr) - x));
+                }
             }
         }
         cp_async_wait_all();
@@ -509,10 +529,19 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         }
 
         if (copy_ok && gg < nst) {
-            uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
-            for (int ll = 0; ll < Q; ++ll) {
-                const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
-                for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * G]);
+            if constexpr (SYS) {
+                uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
+                for (int ll = 0; ll < Q; ++ll) {
+                    const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
+                    uint64_t *o = out + (int64_t)grp().lpos[ll] * P;
+                    for (int x = xk; x < P; x += XK) __stcs(o + x, buf[x * G]);
+                }
+            } else {
+                uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+                for (int ll = 0; ll < Q; ++ll) {
+                    const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
+                    for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * G]);
+                }
             }
         }
         __syncwarp();
@@ -924,6 +953,74 @@ __global__ void __launch_bounds__(32) decode_stream(const __grid_constant__ DecP
     });
 }
 
+// ---------------------------------------------------------------------------
+// sys_residual: first pass of a systematic decode. For every lost data line
+// j (image row lpos[j]) and column x: the bin of the projection dedicated to
+// the front that rebuilds x (direction pp), XOR the known lines' pixels of
+// that bin's line, (l2, x + (l2 - lpos[j]) pp) -- Eq. 1's sum with the known
+// pixels removed -- written into the lost line itself (its contents are
+// garbage until rebuilt). With one lost line these are its pixels; with more,
+// decode_lines<SYS> then runs the path on those rows. Memory-bound and
+// independent per word: one warp per (stripe, lost line) row, lanes along x
+// (coalesced loads of the bins, the known rows and the store).
+template <bool BATCHED>
+__global__ void __launch_bounds__(256) sys_residual(const __grid_constant__ DecParams a)
+{
+    const int P = a.P, E = a.Q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + a.G - 1) / a.G;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const DecGroup *gr;
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            gr = a.groups + wk.group;
+            nst = wk.nst;
+            first = wk.first;
+        } else {
+            gr = &a.grp;
+            s0 = item * a.G;
+            nst = (int)min64(a.G, a.S - s0);
+        }
+        const uint32_t known = gr->known;
+        for (int row = warp; row < nst * E; row += nwarps) {
+            const int g = row / E, j = row - g * E;
+            const uint64_t *par = BATCHED ? a.srcp[first + g] : a.proj + (s0 + g) * a.total;
+            uint64_t *dat = BATCHED ? a.dstp[first + g] : a.img + (s0 + g) * (int64_t)a.Qd * P;
+            const int lp = gr->lpos[j], sp = gr->split[j];
+            const int pa = gr->p[2 * j], pb = gr->p[2 * j + 1];
+            const int sa = gr->src[2 * j], sb = gr->src[2 * j + 1];
+            for (int x = lane; x < P; x += 32) {
+                const bool left = x < sp;
+                const int pp = left ? pa : pb;
+                uint64_t v = __ldcs(par + ((left ? sa : sb) - x));
+                for (uint32_t k = known; k; k &= k - 1) {
+                    const int l2 = __ffs(k) - 1;
+                    const int x2 = x + (l2 - lp) * pp;
+                    if ((unsigned)x2 < (unsigned)P) v ^= dat[(int64_t)l2 * P + x2];
+                }
+                dat[(int64_t)lp * P + x] = v;
+            }
+        }
+    }
+}
+
+// Launch sys_residual over the same work items as the decode that follows
+// (L.G stripes each, plain form).
+template <bool BATCHED>
+int launch_sys_residual(DecParams &a, const DecodeLayout &L, int64_t nitems, cudaStream_t st)
+{
+    a.G = L.G;
+    if (nitems <= 0) return 0;
+    int dev = 0, sms = 0, err = 0;
+    if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
+    if ((err = record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return err;
+    const int64_t grid = std::min<int64_t>(nitems, (int64_t)sms * 8);
+    sys_residual<BATCHED><<<(unsigned)grid, 256, 0, st>>>(a);
+    return record_cuda(cudaGetLastError());
+}
+
 using DecKernel = void (*)(const DecParams);
 
 template <bool BATCHED>
@@ -954,6 +1051,22 @@ DecKernel pick_lines(int Q)
     case 6: return decode_lines<6, BATCHED>;
     case 7: return decode_lines<7, BATCHED>;
     case 8: return decode_lines<8, BATCHED>;
+    default: return nullptr;
+    }
+}
+
+template <bool BATCHED>
+DecKernel pick_lines_sys(int Q)
+{
+    switch (Q) {
+    case 1: return decode_lines<1, BATCHED, true>;
+    case 2: return decode_lines<2, BATCHED, true>;
+    case 3: return decode_lines<3, BATCHED, true>;
+    case 4: return decode_lines<4, BATCHED, true>;
+    case 5: return decode_lines<5, BATCHED, true>;
+    case 6: return decode_lines<6, BATCHED, true>;
+    case 7: return decode_lines<7, BATCHED, true>;
+    case 8: return decode_lines<8, BATCHED, true>;
     default: return nullptr;
     }
 }
@@ -992,9 +1105,10 @@ DecKernel pick_stream(int Q)
 
 // Launch a decode kernel over `nitems` work items with a layout from
 // decode_layout; a's path and addressing fields are already set.
+// sys: the systematic form (decode_lines only).
 template <bool BATCHED>
 int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig &cfg,
-                         int64_t nitems, cudaStream_t st)
+                         int64_t nitems, cudaStream_t st, bool sys = false)
 {
     a.reach = L.reach;
     a.RP = L.RP;
@@ -1008,7 +1122,9 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     if (const char *e = getenv("MOJETTE_DECODE_STEADY")) a.steady = atoi(e) ? 1 : 0;
     else a.steady = 1;
     if (nitems <= 0) return 0;
-    DecKernel fn = L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
+    if (sys && L.kernel != 0) return -EINVAL;
+    DecKernel fn = sys ? pick_lines_sys<BATCHED>(a.Q)
+                 : L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
                  : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
                                  : pick_fronts<BATCHED>(a.Q);

@@ -25,6 +25,10 @@ constexpr uint32_t kStatusWaitTimeout = 1u;
 constexpr uint32_t kStepSteady = 1u << 31;
 constexpr int kFastMaxLines = 15;
 
+// Most lost data lines a systematic decode rebuilds in one stripe (one lane
+// pair per lost line in decode_lines).
+constexpr int kSysMaxLines = 8;
+
 // decode_stream stages and writes a stripe in this many chunks of columns,
 // by distance from the nearer end of each line's front.
 constexpr int kStreamChunks = 4;
@@ -38,6 +42,13 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 struct Schedule {
     uint32_t mask = 0;
     int T = 0;                       // number of steps
+    // Lines the path rebuilds: every line (lines = Q, lpos[l] = l), or for a
+    // systematic plan the lost data lines (image rows lpos[0] < lpos[1] <
+    // ...; line indices below count these), the rows in `known` being read
+    // from the data instead. lines = 0: nothing to rebuild.
+    int lines = 0;
+    int32_t lpos[kMaxLines] = {};
+    uint32_t known = 0;
     uint32_t fwd = 0;                // operand pattern of the steady steps
     int32_t projL[kMaxLines] = {};   // projection rebuilding line l left of split
     int32_t projR[kMaxLines] = {};   // ... and from split rightwards
@@ -83,6 +94,10 @@ struct EncodeConfig {
 
 struct Plan {
     int P = 0, Q = 0, n = 0;
+    // Systematic form: the Q data lines are packets themselves and the n
+    // projections are parity packets; erasure mask bit l < Q marks data
+    // line l lost, bit Q + i projection i.
+    bool systematic = false;
     int32_t p[kMaxProj] = {};
     int64_t B[kMaxProj] = {};
     int64_t off[kMaxProj] = {};
@@ -149,7 +164,11 @@ struct DecodeArgs {
     uint64_t *img;
     int64_t S;
     int64_t total;
-    int P, Q;
+    int P, Q;                       // Q: lines rebuilt (systematic: lost lines)
+    bool sys;                       // systematic: img holds the Qd data lines, in place
+    int Qd;                         // data lines per stripe
+    int32_t lpos[kMaxLines];        // image row of each rebuilt line
+    uint32_t known;                 // systematic: rows read from img
     int T;
     const uint32_t *steps;          // device
     uint32_t fwd;                   // operand pattern of the steady steps
@@ -173,6 +192,8 @@ struct DecGroup {
     int32_t chunk_w;                // streamed chunks (see Schedule)
     int32_t chunk_wait[kStreamChunks];
     int32_t chunk_done[kStreamChunks];
+    int32_t lpos[kMaxLines];        // image row of each rebuilt line
+    uint32_t known;                 // systematic: data rows read, not rebuilt
 };
 
 // One work item of a batched decode: nst (<= G) stripes of group `group`,
@@ -192,14 +213,17 @@ struct DecodeLayout {
     int rowbase[kMaxLines];   // first column of each line's row
     int64_t smem;       // dynamic shared memory per CTA
 };
-// rowoff: decode_lines row offsets (may be null: none).
-int decode_layout(int P, int Q, int maxp, int maxT, const DecodeConfig &cfg, const int32_t *rowoff,
-                  DecodeLayout *L);
+// Q lines rebuilt whose image rows span `span` rows (Q - 1 unless
+// systematic); rowoff: decode_lines row offsets (may be null: none).
+int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig &cfg,
+                  const int32_t *rowoff, DecodeLayout *L);
 // Bank slots of one stripe group of decode_lines / decode_stream for Q lines.
 int decode_bank_slots(int Q);
 
 struct DecBatchArgs {
-    int P, Q;
+    int P, Q;                       // Q: lines rebuilt (systematic: lost lines)
+    bool sys;                       // systematic: dstp[s] holds the Qd data lines, in place
+    int Qd, span;
     int maxp, maxT;                 // over the groups (layout)
     int32_t rowoff[kMaxLines];      // decode_lines row offsets for the launch
     const DecGroup *groups;         // device

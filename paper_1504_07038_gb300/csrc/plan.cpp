@@ -44,9 +44,16 @@ namespace {
 // every front move one column per step, so a sweep takes about P/2 steps.
 // Fills `out` and returns the number of steps, or -1 if the sweep stalls or
 // reaches `limit` steps.
-int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
+//
+// The lines swept need not be all the image's rows: a systematic decode
+// rebuilds only the lost data lines, after removing the known lines from the
+// bins, so that the sweep runs over Q = `lines` lines at image rows pos[0] <
+// pos[1] < ... (all rows 0 .. Q-1 otherwise); the other pixel of a bin line
+// on line l2 is then (l2, x + (pos[l2] - pos[l]) p).
+int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines, int limit,
+          Schedule *out)
 {
-    const int P = pl.P, Q = pl.Q;
+    const int P = pl.P, Q = lines;
     int32_t pF[2][kMaxLines];
     for (int l = 0; l < Q; ++l) {
         pF[0][l] = pl.p[asc[l]];
@@ -71,7 +78,7 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
                 bool ready = true;
                 for (int l2 = 0; l2 < Q && ready; ++l2) {
                     if (l2 == l) continue;
-                    const int64_t x2 = (int64_t)x + (int64_t)(l2 - l) * p;
+                    const int64_t x2 = (int64_t)x + (int64_t)(pos[l2] - pos[l]) * p;
                     if (x2 < 0 || x2 >= P) continue;
                     if (known[(size_t)l2 * P + x2]) continue;
                     if (l2 == l + 1 && took[side][l2] == x2) continue;
@@ -92,7 +99,7 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
         for (int side = 0; side < 2; ++side)
             for (int l = 0; l + 1 < Q; ++l) {
                 if (took[side][l] < 0) continue;
-                const int64_t x2 = (int64_t)took[side][l] + pF[side][l];
+                const int64_t x2 = (int64_t)took[side][l] + (int64_t)(pos[l + 1] - pos[l]) * pF[side][l];
                 if (x2 >= 0 && x2 < P && took[side][l + 1] == x2) fwd |= 1u << (2 * l + side);
             }
         pattern.push_back(fwd);
@@ -156,6 +163,9 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
         }
     }
     out->fwd = fwd;
+    out->lines = Q;
+    out->known = 0;
+    for (int l = 0; l < Q; ++l) out->lpos[l] = pos[l];
     out->T = (int)steps.size();
     out->steps = std::move(steps);
     out->fwdw = std::move(pattern);
@@ -172,8 +182,8 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
         // front's first pixel plus that pixel's x (a front reads one run of
         // consecutive bins, all stored, hence consecutive stored words)
         if (!pl.trimmed) {
-            out->srcL[l] = pl.off[iL] + (int64_t)l * pl.p[iL] - pl.bmin[iL];
-            out->srcR[l] = pl.off[iR] + (int64_t)l * pl.p[iR] - pl.bmin[iR];
+            out->srcL[l] = pl.off[iL] + (int64_t)pos[l] * pl.p[iL] - pl.bmin[iL];
+            out->srcR[l] = pl.off[iR] + (int64_t)pos[l] * pl.p[iR] - pl.bmin[iR];
         } else {
             const int sp = a[l];
             auto stored = [&](int i, int64_t j) {
@@ -201,7 +211,7 @@ int sweep(const Plan &pl, const std::vector<int> &asc, int limit, Schedule *out)
 void choose_row_phases(const Plan &pl, Schedule *sc)
 {
     sc->phases_done = true;
-    const int P = pl.P, Q = pl.Q;
+    const int P = pl.P, Q = sc->lines;
     for (int l = 0; l < kMaxLines; ++l) sc->rowoff[l] = 0;
     if (Q < 2 || Q > 8) return;
     const int G = std::max(1, 32 / (2 * Q));
@@ -231,7 +241,8 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
                 for (int k = 0; k < Q - 1; ++k) {
                     const int l2 = (l + 1 + k) % Q;
                     const bool fwd = (k == 0 && l + 1 < Q && ((f >> fr) & 1u));
-                    a[(1 + k) * 2 * Q + fr] = fwd ? Acc{-1, 0} : Acc{(int8_t)l2, (int16_t)(xx + (l2 - l) * p)};
+                    a[(1 + k) * 2 * Q + fr] =
+                        fwd ? Acc{-1, 0} : Acc{(int8_t)l2, (int16_t)(xx + (sc->lpos[l2] - sc->lpos[l]) * p)};
                 }
             }
         for (int l = 0; l < Q; ++l)
@@ -305,45 +316,92 @@ constexpr int kMaxCandidates = 512;
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
 {
     if (pl.Q > kMaxLines) return -EINVAL;
+    // Lines to rebuild (image rows, ascending) and surviving projections.
+    // Non-systematic: every line, from any Q of the n projections.
+    // Systematic: the lost data lines (mask bits 0 .. Q-1), each with one of
+    // the surviving parity projections (mask bits Q .. Q+n-1).
+    int pos[kMaxLines];
+    int L = 0;
     std::vector<int> surv;
-    for (int i = 0; i < pl.n; ++i)
-        if (!(mask >> i & 1u)) surv.push_back(i);
-    if ((int)surv.size() < pl.Q) return -ENOTRECOVERABLE;
+    if (pl.systematic) {
+        for (int l = 0; l < pl.Q; ++l)
+            if (mask >> l & 1u) pos[L++] = l;
+        for (int i = 0; i < pl.n; ++i)
+            if (!(mask >> (pl.Q + i) & 1u)) surv.push_back(i);
+        if (L == 0) {
+            // nothing lost: the data lines are the image, no path
+            *out = Schedule();
+            out->mask = mask;
+            out->lines = 0;
+            out->known = (pl.Q >= 32 ? 0xFFFFFFFFu : (1u << pl.Q) - 1u);
+            out->phases_done = true;
+            return 0;
+        }
+        if (L > kSysMaxLines) return -EINVAL;
+    } else {
+        for (int l = 0; l < pl.Q; ++l) pos[L++] = l;
+        for (int i = 0; i < pl.n; ++i)
+            if (!(mask >> i & 1u)) surv.push_back(i);
+    }
+    if ((int)surv.size() < L) return -ENOTRECOVERABLE;
 
-    // Any Q survivors rebuild the same image (Eq. 3 gives uniqueness); pick
-    // the subset with the fewest steps. Candidates are enumerated with the
-    // smallest |p| first.
+    // Any L survivors rebuild the same lines (Eq. 3 gives uniqueness; for
+    // the systematic form, the generalised Vandermonde argument of the
+    // oracle's tests); pick the subset with the fewest steps. Candidates
+    // are enumerated with the smallest |p| first.
     std::stable_sort(surv.begin(), surv.end(), [&](int x, int y) {
         const int ax = pl.p[x] < 0 ? -pl.p[x] : pl.p[x];
         const int ay = pl.p[y] < 0 ? -pl.p[y] : pl.p[y];
         return ax < ay;
     });
-    const int m = (int)surv.size(), Q = pl.Q;
-    std::vector<int> pick(Q);
+    const int m = (int)surv.size();
+    std::vector<int> pick(L);
     std::iota(pick.begin(), pick.end(), 0);
     int best = -1;
     Schedule tmp;
     int tried = 0;
     while (true) {
-        std::vector<int> asc(Q);
-        for (int k = 0; k < Q; ++k) asc[k] = surv[pick[k]];
+        std::vector<int> asc(L);
+        for (int k = 0; k < L; ++k) asc[k] = surv[pick[k]];
         std::sort(asc.begin(), asc.end(), [&](int x, int y) { return pl.p[x] < pl.p[y]; });
+        if (pl.systematic && L == 1) {
+            // one lost line: once the known lines are removed every bin of
+            // the projection holds one lost pixel, so no step is needed
+            tmp = Schedule();
+            const int i = asc[0];
+            tmp.lines = 1;
+            tmp.lpos[0] = pos[0];
+            tmp.projL[0] = tmp.projR[0] = i;
+            tmp.pL[0] = tmp.pR[0] = pl.p[i];
+            tmp.split[0] = pl.P;
+            tmp.srcL[0] = tmp.srcR[0] = pl.off[i] + (int64_t)pos[0] * pl.p[i] - pl.bmin[i];
+            tmp.T = 0;
+            best = 0;
+            *out = tmp;
+            break;
+        }
         const int limit = best < 0 ? (1 << 30) : best;
-        const int T = sweep(pl, asc, limit, &tmp);
+        const int T = sweep(pl, asc, pos, L, limit, &tmp);
         if (T >= 0 && (best < 0 || T < best)) {
             best = T;
             *out = tmp;
         }
         if (++tried >= kMaxCandidates) break;
-        // next combination of Q out of m
-        int k = Q - 1;
-        while (k >= 0 && pick[k] == m - Q + k) --k;
+        // next combination of L out of m
+        int k = L - 1;
+        while (k >= 0 && pick[k] == m - L + k) --k;
         if (k < 0) break;
         ++pick[k];
-        for (int r = k + 1; r < Q; ++r) pick[r] = pick[r - 1] + 1;
+        for (int r = k + 1; r < L; ++r) pick[r] = pick[r - 1] + 1;
     }
     if (best < 0) return -ENOTRECOVERABLE;
     out->mask = mask;
+    if (pl.systematic) {
+        uint32_t known = 0;
+        for (int l = 0; l < pl.Q; ++l)
+            if (!(mask >> l & 1u)) known |= 1u << l;
+        out->known = known;
+    }
     out->dev.clear();
     return 0;
 }
@@ -394,7 +452,7 @@ int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev)
     std::vector<uint32_t> both(2 * n);
     std::copy(sc.steps.begin(), sc.steps.end(), both.begin());
     std::copy(sc.fwdw.begin(), sc.fwdw.end(), both.begin() + n);
-    if ((r = record_cuda(cudaMemcpy(d, both.data(), 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice)))) {
+    if (n && (r = record_cuda(cudaMemcpy(d, both.data(), 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice)))) {
         cudaFree(d);
         return r;
     }

@@ -337,7 +337,9 @@ int mojette_server_submit(mojette_server_t server, const mojette_request_t *reqs
         if (r.op != MOJETTE_OP_ENCODE && r.op != MOJETTE_OP_DECODE) return -EINVAL;
         const Plan *pl = reinterpret_cast<const Plan *>(r.plan);
         if (r.op == MOJETTE_OP_DECODE) {
-            if (pl->Q > kMaxLines) return -EINVAL;
+            // a systematic read rebuilds lines in place from two inputs
+            // (data and parity): not a request of this server
+            if (pl->Q > kMaxLines || pl->systematic) return -EINVAL;
             if (pl->n < 32 && (r.erasure_mask >> pl->n)) return -EINVAL;
             int err = 0;
             if (!get_schedule(*const_cast<Plan *>(pl), r.erasure_mask, &err)) return err;

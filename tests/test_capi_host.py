@@ -220,3 +220,151 @@ def test_plan_config_round_trip(tmp_path):
     with pytest.raises(mj.MojetteError) as ei:
         mj.mojette_plan_config(b, {"decode_tuned": 1, "decode_kernel": 0, "decode_gpc": 0})
     assert ei.value.code == -errno.EINVAL
+
+
+# ------------------------------------------------------- systematic form --
+
+SYS_CONFIGS = [
+    (128, 4, [-1, 1]),
+    (256, 4, [-1, 1]),
+    (64, 8, [-2, -1, 1, 2]),
+    (128, 8, [-2, -1, 1, 2]),
+]
+
+
+def sys_replay(sched, plan, data, parity, P, Q, p, mask):
+    """Run a systematic schedule on the CPU and return the rebuilt lost lines
+    (uint64[S, lines, P]).
+
+    The lost lines (image rows lpos) first get their dedicated bins with the
+    known lines' pixels removed; then the steps rebuild each pixel from that
+    residual bin XOR the other lost lines' pixels of its bin line, each
+    rebuilt at an earlier step or -- for line l + 1 only -- by the same front
+    earlier in the same step."""
+    lpos = [l for l in range(Q) if mask >> l & 1]
+    known = [l for l in range(Q) if not mask >> l & 1]
+    L = len(lpos)
+    assert sched["lines"] == L
+    S = data.shape[0]
+    left, right, split = sched["left"], sched["right"], sched["split"]
+    for i in set(left) | set(right):
+        assert not mask >> (Q + i) & 1                    # lost parity never read
+    res = np.zeros((S, L, P), dtype=np.uint64)
+    for j in range(L):
+        for x in range(P):
+            i = left[j] if x < split[j] else right[j]
+            pi = p[i]
+            bmin = -(P - 1) + min(0, (Q - 1) * pi)
+            v = parity[:, plan.offsets[i] + (lpos[j] * pi - x - bmin)].copy()
+            for l2 in known:
+                x2 = x + (l2 - lpos[j]) * pi
+                if 0 <= x2 < P:
+                    v ^= data[:, l2, x2]
+            res[:, j, x] = v
+    out = np.zeros_like(res)
+    step_of = np.full((L, P), -1)
+    front_of = np.full((L, P), -1)
+    xa, xz = [0] * L, [P - 1] * L
+    if sched["T"] == 0:                  # one lost line: the residual bins are its pixels
+        assert L == 1 and split[0] == P
+        return res
+    for t, w in enumerate(sched["steps"]):
+        for side in (0, 1):
+            for l in range(L - 1, -1, -1):
+                if not (w >> (2 * l + side) & 1):
+                    continue
+                x = xa[l] if side == 0 else xz[l]
+                pi = p[left[l] if side == 0 else right[l]]
+                assert (x < split[l]) == (side == 0) and step_of[l, x] < 0
+                v = res[:, l, x].copy()
+                for l2 in range(L):
+                    x2 = x + (lpos[l2] - lpos[l]) * pi
+                    if l2 == l or not 0 <= x2 < P:
+                        continue
+                    done = step_of[l2, x2]
+                    ok = 0 <= done < t or (done == t and l2 == l + 1 and front_of[l2, x2] == side)
+                    assert ok, (t, side, l, x, l2, x2, done)
+                    v ^= out[:, l2, x2]
+                if l + 1 < L:
+                    x2 = x + (lpos[l + 1] - lpos[l]) * pi
+                    fwd_here = bool(0 <= x2 < P and step_of[l + 1, x2] == t and front_of[l + 1, x2] == side)
+                    assert bool(sched["forward"][t] >> (2 * l + side) & 1) == fwd_here
+                out[:, l, x] = v
+                step_of[l, x] = t
+                front_of[l, x] = side
+                if side == 0:
+                    xa[l] += 1
+                else:
+                    xz[l] -= 1
+    assert (step_of >= 0).all()
+    return out
+
+
+def _sys_masks(Q, r, limit=None, seed=3):
+    ms = [m for m in range(1 << (Q + r)) if bin(m).count("1") <= r and m & ((1 << Q) - 1)]
+    if limit and len(ms) > limit:
+        ms = [ms[i] for i in np.random.default_rng(seed).choice(len(ms), limit, replace=False)]
+    return ms
+
+
+@pytest.mark.parametrize("P,Q,p", SYS_CONFIGS)
+def test_sys_schedules_replay_to_the_image(P, Q, p):
+    plan = mj.Plan(P, Q, p, systematic=True)
+    img = inputs.stripes(2, Q, P, seed=13)
+    par = oracle.encode(img, p)
+    for m in _sys_masks(Q, len(p), limit=60):
+        sched = mj.mojette_schedule(plan, m)
+        lost = [l for l in range(Q) if m >> l & 1]
+        assert sched["T"] <= P // 2 + 2 * Q * max(abs(v) for v in p)
+        data = img.copy()
+        data[:, lost] = np.uint64(7)
+        got = sys_replay(sched, plan, data, par, P, Q, p, m)
+        assert (got == img[:, lost]).all(), m
+
+
+def test_sys_schedule_for_every_small_geometry():
+    """Exhaustive over tiny geometries: every mask losing e data lines with at
+    least e parity projections left yields a path that rebuilds them."""
+    rng = np.random.default_rng(17)
+    for P in range(1, 9):
+        for Q in range(1, 6):
+            for _ in range(2):
+                r = int(rng.integers(1, 4))
+                p = sorted(rng.choice(np.arange(-5, 6), size=r, replace=False).tolist())
+                plan = mj.Plan(P, Q, p, systematic=True)
+                img = inputs.stripes(2, Q, P, seed=P * 10 + Q)
+                par = oracle.encode(img, p)
+                for m in range(1 << (Q + r)):
+                    e = bin(m & ((1 << Q) - 1)).count("1")
+                    surv = r - bin(m >> Q).count("1")
+                    if e == 0 or e > surv:
+                        continue
+                    sched = mj.mojette_schedule(plan, m)
+                    lost = [l for l in range(Q) if m >> l & 1]
+                    got = sys_replay(sched, plan, img, par, P, Q, p, m)
+                    assert (got == img[:, lost]).all(), (P, Q, p, m)
+
+
+def test_sys_calls_validate_arguments_without_a_device():
+    L = mj.lib()
+    sysp = mj.Plan(16, 4, [-1, 1], systematic=True)
+    plain = mj.mojette_plan(16, 4, [-2, -1, 1, 2])
+    assert L.mojette_sys_decode(plain.handle, 16, 1, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_decode(sysp.handle, 16, 1, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_decode_noalloc(sysp.handle, 16, 1, 16, 1, None) == -errno.EINVAL
+    assert L.mojette_sys_decode(sysp.handle, 16, 1 << 6, 16, 1, None) == -errno.EINVAL   # bit beyond Q + n
+    assert L.mojette_sys_decode(sysp.handle, 16, 0b0111, 16, 1, None) == -errno.ENOTRECOVERABLE
+    assert L.mojette_sys_decode(sysp.handle, 16, 0b0011 | 1 << 4, 16, 1, None) == -errno.ENOTRECOVERABLE
+    assert L.mojette_sys_decode(sysp.handle, 16, 0b0101, 24, 1, None) == -errno.ERANGE
+    assert L.mojette_sys_decode(sysp.handle, 0, 3 << 4, 0, 1, None) == 0     # no line lost: nothing to do
+    assert L.mojette_sys_decode(sysp.handle, 16, 0b0001, 16, 0, None) == 0   # S = 0
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int * 2)(-1, 1)
+    both = mj.MOJETTE_PLAN_SYSTEMATIC | mj.MOJETTE_PLAN_TRIM_UNUSED
+    assert L.mojette_plan_ex(16, 4, arr, 2, both, ctypes.byref(h)) == -errno.EINVAL
+    wide = (ctypes.c_int * 4)(-2, -1, 1, 2)
+    assert L.mojette_plan_ex(16, 29, wide, 4, mj.MOJETTE_PLAN_SYSTEMATIC, ctypes.byref(h)) == -errno.EINVAL
+    nine = (ctypes.c_int * 9)(*range(-4, 5))
+    assert L.mojette_plan_ex(16, 12, nine, 9, mj.MOJETTE_PLAN_SYSTEMATIC, ctypes.byref(h)) == 0
+    assert L.mojette_sys_decode(h.value, 16, (1 << 9) - 1, 16, 1, None) == -errno.EINVAL   # 9 lines lost
+    L.mojette_plan_destroy(h.value)
