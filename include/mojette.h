@@ -121,7 +121,9 @@ int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin);
  * restored across processes). 8 words each:
  *   [0] 1: decode configuration set (tuned), 0: library defaults;
  *   [1] decode kernel (0 decode_lines, 1 decode_fronts, 2 decode_stream,
- *       3 decode_cols; Q > 8 allows 1 only);
+ *       3 decode_cols, 4 decode_scan2 -- the closed form for two rebuilt
+ *       lines, the default where it applies; Q > 8 allows 1 only, 4 needs
+ *       Q = 2 or a systematic plan and applies only to two-line decodes);
  *   [2] work items per CTA (1 .. 64); [3] persistent grid (0/1);
  *   [4] decode_lines row phases (0/1);
  *   [5] 1: encode configuration set; [6] encode tile bytes (0: by Q);
@@ -359,7 +361,7 @@ int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps)
  *   configs     6 words per launch: op, Q (decode: lines rebuilt per
  *               stripe, a systematic launch's lost lines), P, then for decode the kernel
  *               (0 decode_lines, 1 decode_fronts, 2 decode_stream,
- *               3 decode_cols), work
+ *               3 decode_cols, 4 decode_scan2), work
  *               items per CTA and
  *               flags (bit 0 persistent grid, bit 1 bank-phased rows),
  *               for encode 0, the tile bytes (0 = default) and 0. The array

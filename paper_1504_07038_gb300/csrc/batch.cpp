@@ -37,6 +37,7 @@ struct Klass {
     int lines = 0;                  // lines rebuilt per stripe (systematic: lost lines)
     int span = 0;                   // widest row distance between two of them
     bool sys = false;               // systematic plan: in-place decode of the lost lines
+    bool scan_ok = false;           // two lines and every group has the closed form (decode_scan2)
     int32_t rowoff[kMaxLines] = {};   // row phases of its largest group
     DecodeConfig dcfg;
     EncodeConfig ecfg;
@@ -108,7 +109,8 @@ int fill_work(Batch &b, Klass &k, int G)
 
 int class_layout(const Klass &k, const DecodeConfig &cfg, DecodeLayout *L)
 {
-    if (k.sys && cfg.kernel != 0) return -EINVAL;   // decode_lines only
+    if (k.sys && cfg.kernel != 0 && cfg.kernel != 4) return -EINVAL;   // decode_lines or decode_scan2
+    if (cfg.kernel == 4 && !k.scan_ok) return -EINVAL;
     return decode_layout(k.plan->P, k.lines, k.span, k.maxp, k.maxT, cfg, k.rowoff, L);
 }
 
@@ -282,10 +284,9 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         if (k.op == MOJETTE_OP_ENCODE) {
             k.ecfg = k.plan->tuned_enc ? k.plan->enc_cfg : EncodeConfig();
         } else {
-            k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : DecodeConfig();
-            if (k.sys && k.dcfg.kernel != 0) k.dcfg = DecodeConfig();
             k.lines = k.sys ? kl : k.plan->Q;
             k.gbase = (int64_t)groups.size();
+            k.scan_ok = k.lines == 2;
             int64_t big = 0;
             Schedule *big_sc = nullptr;
             for (int64_t g = r; g < e;) {
@@ -303,6 +304,11 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 gr.fwd = sc->fwd;
                 gr.known = sc->known;
                 for (int l = 0; l < sc->lines; ++l) gr.lpos[l] = sc->lpos[l];
+                k.scan_ok = k.scan_ok && sc->scan2;
+                for (int j = 0; j < 2; ++j) {
+                    gr.scan_p[j] = sc->scan_p[j];
+                    gr.scan_src[j] = (int32_t)sc->scan_src[j];
+                }
                 k.span = std::max(k.span, sc->lines > 0 ? sc->lpos[sc->lines - 1] - sc->lpos[0] : 0);
                 for (int l = 0; l < sc->lines; ++l) {
                     gr.p[2 * l] = sc->pL[l];
@@ -325,6 +331,14 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 groups.push_back(gr);
                 k.gcount.push_back(h - g);
                 g = h;
+            }
+            // configuration: the plan's tuned one where it applies, else the
+            // closed form for two lines, else decode_lines
+            k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : DecodeConfig();
+            if (!k.plan->tuned_dec && k.scan_ok) k.dcfg.kernel = 4;
+            if ((k.sys && k.dcfg.kernel != 0 && k.dcfg.kernel != 4) || (k.dcfg.kernel == 4 && !k.scan_ok)) {
+                k.dcfg = DecodeConfig();
+                if (k.scan_ok) k.dcfg.kernel = 4;
             }
             if (big_sc && k.count >= kPhaseMinStripes) {
                 const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
@@ -396,8 +410,8 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
         if (k.op == MOJETTE_OP_DECODE) {
             DecodeLayout L;
             if ((err = class_layout(k, k.dcfg, &L))) {
-                // a tuned configuration that no longer fits: the defaults,
-                // else decode_fronts (G down to one stripe; not for the
+                // a configuration that does not fit: decode_lines, else
+                // decode_fronts (G down to one stripe; not for the
                 // systematic form)
                 k.dcfg = DecodeConfig();
                 if ((err = class_layout(k, k.dcfg, &L))) {
@@ -488,6 +502,8 @@ int tune(Batch &b, cudaStream_t st, int reps)
         } else {
             struct Cand { int kernel, gpc, persist, rowoff; };
             std::vector<Cand> cands;
+            if (k.scan_ok)
+                for (int g : {1, 2, 4, 8}) cands.push_back({4, g, 0, 0});
             if (k.sys) {
                 for (int sp : {0, 1})
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});

@@ -66,6 +66,11 @@ static void fill_decode_args(const Plan &pl, const Schedule &sc, int64_t S, Deco
         a->chunk_wait[c] = sc.chunk_wait[c];
         a->chunk_done[c] = sc.chunk_done[c];
     }
+    a->scan2 = sc.scan2;
+    for (int j = 0; j < 2; ++j) {
+        a->scan_p[j] = sc.scan_p[j];
+        a->scan_src[j] = sc.scan_src[j];
+    }
 }
 
 // Erasure mask bits a plan defines: n projections, or for a systematic plan
@@ -171,9 +176,10 @@ int mojette_plan_config(mojette_plan_t plan, int32_t *get, const int32_t *set)
     }
     if (set) {
         if (set[0]) {
-            if (set[1] < 0 || set[1] > 3 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
+            if (set[1] < 0 || set[1] > 4 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
                 return -EINVAL;
             if (set[1] != 1 && pl->Q > 8) return -EINVAL;
+            if (set[1] == 4 && pl->Q != 2 && !pl->systematic) return -EINVAL;
             pl->dec_cfg.kernel = set[1];
             pl->dec_cfg.gpc = set[2];
             pl->dec_cfg.persist = set[3];

@@ -32,6 +32,18 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
     for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = L->reach + l * L->RP;
     const int want = (cfg.kernel == 1 || Q > 8) ? 1 : cfg.kernel;
     L->kernel = want;
+    if (want == 4) {
+        // decode_scan2: two lines, one warp per stripe, kScanWarps per CTA
+        if (Q != 2) return -EINVAL;
+        L->G = kScanWarps;
+        L->GS = L->G;
+        L->reach = 0;
+        L->RP = P;
+        L->TS = 0;
+        L->SWc = scan2_words(P);
+        L->smem = (int64_t)L->G * L->SWc * 8;
+        return L->smem > cap ? -EINVAL : 0;
+    }
     if (want == 2) {
         // decode_stream: rows packed at pitch P (operands outside the image
         // read one zero column after the rows), step and forward words first
@@ -134,31 +146,50 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         a.grp.chunk_wait[c] = d.chunk_wait[c];
         a.grp.chunk_done[c] = d.chunk_done[c];
     }
+    for (int j = 0; j < 2; ++j) {
+        a.grp.scan_p[j] = d.scan_p[j];
+        a.grp.scan_src[j] = (int32_t)d.scan_src[j];
+    }
 
-    // decode_lines for Q <= 8 unless MOJETTE_DECODE_KERNEL names another
+    // decode_scan2 for two lines, decode_lines for Q <= 8, unless
+    // MOJETTE_DECODE_KERNEL names another
     DecodeConfig cfg;
+    if (d.scan2) cfg.kernel = 4;
     if (const char *kenv = getenv("MOJETTE_DECODE_KERNEL")) {
-        if (strcmp(kenv, "fronts") == 0) cfg.kernel = 1;
+        if (strcmp(kenv, "lines") == 0) cfg.kernel = 0;
+        else if (strcmp(kenv, "fronts") == 0) cfg.kernel = 1;
         else if (strcmp(kenv, "stream") == 0) cfg.kernel = 2;
         else if (strcmp(kenv, "cols") == 0) cfg.kernel = 3;
+        else if (strcmp(kenv, "scan") == 0 && d.scan2) cfg.kernel = 4;
     }
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
     if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;
     DecodeLayout L;
     if (d.sys) {
-        // the systematic form: residual bins into the lost rows, then the
-        // path on them (decode_lines only; none needed for one lost line)
-        cfg.kernel = 0;
+        // the systematic form: two lost lines in closed form (decode_scan2,
+        // which removes the known lines itself); otherwise residual bins
+        // into the lost rows, then the path on them (decode_lines; no path
+        // for one lost line)
+        if (cfg.kernel != 4) cfg.kernel = 0;
         const int span = d.lpos[d.Q - 1] - d.lpos[0];
         int err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
+        if (err == -EINVAL && cfg.kernel == 4) {
+            cfg.kernel = 0;
+            err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
+        }
         if (err) return err;
         const int64_t nitems = (d.S + L.G - 1) / L.G;
+        if (L.kernel == 4) return launch_decode_kernel<false>(a, L, cfg, nitems, st, true);
         if ((err = launch_sys_residual<false>(a, L, nitems, st))) return err;
         if (d.T == 0) return 0;
         return launch_decode_kernel<false>(a, L, cfg, nitems, st, true);
     }
     int err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
+    if (err == -EINVAL && cfg.kernel == 4) {
+        cfg.kernel = 0;
+        err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
+    }
     if (err == -EINVAL && cfg.kernel != 1) {
         // a warp's G stripes do not fit in shared memory: decode_fronts sizes
         // G to what fits, down to one stripe

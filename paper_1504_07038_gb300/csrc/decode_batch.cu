@@ -8,7 +8,7 @@ namespace mojette {
 int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaStream_t st)
 {
     DecodeLayout L;
-    if (b.sys && cfg.kernel != 0) return -EINVAL;
+    if (b.sys && cfg.kernel != 0 && cfg.kernel != 4) return -EINVAL;
     int err = decode_layout(b.P, b.Q, b.span, b.maxp, b.maxT, cfg, b.rowoff, &L);
     if (err) return err;
     DecParams a;
@@ -21,8 +21,9 @@ int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaSt
     a.P = b.P;
     a.Q = b.Q;
     a.Qd = b.Qd;
-    if (b.sys) {
-        // residual bins into the lost rows, then the path (none for one lost line)
+    if (b.sys && L.kernel != 4) {
+        // residual bins into the lost rows, then the path (none for one lost
+        // line); decode_scan2 removes the known lines itself
         if ((err = launch_sys_residual<true>(a, L, b.nwork, st))) return err;
         if (b.maxT == 0) return 0;
     }

@@ -954,6 +954,165 @@ __global__ void __launch_bounds__(32) decode_stream(const __grid_constant__ DecP
 }
 
 // ---------------------------------------------------------------------------
+// decode_scan2: the inverse for exactly two unknown lines -- a two-line image
+// (Q = 2), or a systematic stripe that lost two data lines -- in closed form
+// instead of a step-by-step path. Lines u (image row l1) and v (row l2 =
+// l1 + d) with projections a and b, p_a < p_b, each over its whole line.
+// With the known lines removed (systematic), Eq. 1 leaves in the bin of
+// pixel (l1, x) of projection a:  Ra(x) = u[x] ^ v[x + d p_a]  and in the
+// bin of pixel (l2, y) of projection b:  Rb(y) = v[y] ^ u[y - d p_b]
+// (a term outside the image absent). Substituting v gives
+//     u[x] = c(x) ^ link(x) u[x - s],   s = d (p_b - p_a) >= 1,
+// with c(x) = Ra(x) ^ Rb(x + d p_a) when x + d p_a is inside the image (else
+// Ra(x), and no link), link(x) also needing x >= s: a prefix XOR along each
+// chain x, x - s, x - 2s, ... cut where a link is missing. It is evaluated by
+// pointer doubling -- round r joins each element to the one s 2^r before it
+// while its chain continues, ceil(log2(P / s)) rounds -- and then
+// v[y] = Rb(y) ^ u[y - d p_b]. The values are those of the Sec. 2.2 inverse
+// (the image is unique); the work is independent per element, so the kernel
+// is bound by memory traffic, not by a chain of ~P/2 dependent steps.
+// One warp per stripe (kScanWarps stripes per work item and CTA); per warp
+// the shared memory holds two copies of u (ping-pong), Rb, and two rows of
+// chain flags.
+__host__ __device__ inline int scan2_words(int P) { return 3 * P + (2 * P + 7) / 8; }
+constexpr int kScanBatch = 8;
+
+template <bool BATCHED, bool SYS>
+__global__ void __launch_bounds__(32 * kScanWarps) decode_scan2(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    const int P = a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *U0 = sm + (size_t)warp * scan2_words(P);
+    uint64_t *U1 = U0 + P, *V = U1 + P;
+    uint8_t *F0 = reinterpret_cast<uint8_t *>(V + P), *F1 = F0 + P;
+
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + a.G - 1) / a.G;
+    for_items(a, nitems, [&](int64_t item) {
+        const DecGroup *gr;
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            gr = a.groups + wk.group;
+            nst = wk.nst;
+            first = wk.first;
+        } else {
+            gr = &a.grp;
+            s0 = item * a.G;
+            nst = (int)min64(a.G, a.S - s0);
+        }
+        if (warp < nst) {
+            const uint64_t *src = BATCHED ? a.srcp[first + warp] : a.proj + (s0 + warp) * a.total;
+            uint64_t *out = BATCHED ? a.dstp[first + warp]
+                                    : a.img + (s0 + warp) * (int64_t)(SYS ? a.Qd : 2) * P;
+            const int l1 = SYS ? gr->lpos[0] : 0, l2 = SYS ? gr->lpos[1] : 1, d = l2 - l1;
+            const int pa = gr->scan_p[0], pb = gr->scan_p[1];
+            const int sa = gr->scan_src[0], sb = gr->scan_src[1];
+            const int s = d * (pb - pa);
+            const uint32_t known = SYS ? gr->known : 0u;
+            // residual bins of both lines (the known lines removed), kScanBatch
+            // columns per lane at a time so that each round of loads -- the
+            // bins, then each known line -- is in flight together
+            for (int x0 = lane; x0 < P; x0 += 32 * kScanBatch) {
+                uint64_t ra[kScanBatch], rb[kScanBatch];
+#pragma unroll
+                for (int c = 0; c < kScanBatch; ++c) {
+                    const int x = x0 + 32 * c;
+                    const bool in = x < P;
+                    ra[c] = in ? __ldcs(src + (sa - x)) : 0ull;
+                    rb[c] = in ? __ldcs(src + (sb - x)) : 0ull;
+                }
+                if constexpr (SYS) {
+                    for (uint32_t k = known; k; k &= k - 1) {
+                        const int l = __ffs(k) - 1;
+                        const uint64_t *row = out + (int64_t)l * P;
+                        uint64_t ta[kScanBatch], tb[kScanBatch];
+#pragma unroll
+                        for (int c = 0; c < kScanBatch; ++c) {
+                            const int x = x0 + 32 * c;
+                            const int xa = x + (l - l1) * pa, xb = x + (l - l2) * pb;
+                            ta[c] = (x < P && (unsigned)xa < (unsigned)P) ? row[xa] : 0ull;
+                            tb[c] = (x < P && (unsigned)xb < (unsigned)P) ? row[xb] : 0ull;
+                        }
+#pragma unroll
+                        for (int c = 0; c < kScanBatch; ++c) {
+                            ra[c] ^= ta[c];
+                            rb[c] ^= tb[c];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < kScanBatch; ++c) {
+                    const int x = x0 + 32 * c;
+                    if (x < P) {
+                        U1[x] = ra[c];
+                        V[x] = rb[c];
+                    }
+                }
+            }
+            __syncwarp();
+            // c(x) and the first links
+            for (int x = lane; x < P; x += 32) {
+                const int y = x + d * pa;
+                const bool in = (unsigned)y < (unsigned)P;
+                const uint64_t vy = V[in ? y : x];          // every index read is in range
+                U0[x] = U1[x] ^ (in ? vy : 0ull);
+                F0[x] = (in && x >= s) ? 1 : 0;
+            }
+            __syncwarp();
+            // pointer doubling along the chains: an element whose chain still
+            // continues (flag set, hence x >= k) takes the XOR of the span k
+            // before it and inherits that span's flag
+            uint64_t *Ui = U0, *Uo = U1;
+            uint8_t *Fi = F0, *Fo = F1;
+            for (int k = s; k < P; k <<= 1) {
+                for (int x0 = lane; x0 < P; x0 += 32 * kScanBatch) {
+                    // flags first, then every partner of the batch at once
+                    bool f[kScanBatch];
+#pragma unroll
+                    for (int c = 0; c < kScanBatch; ++c) {
+                        const int x = x0 + 32 * c;
+                        f[c] = x < P && Fi[x] != 0;
+                    }
+                    uint64_t ux[kScanBatch], uk[kScanBatch];
+                    uint8_t fk[kScanBatch];
+#pragma unroll
+                    for (int c = 0; c < kScanBatch; ++c) {
+                        const int x = x0 + 32 * c;
+                        const int xi = x < P ? x : 0;
+                        const int xk = f[c] ? x - k : xi;
+                        ux[c] = Ui[xi];
+                        uk[c] = Ui[xk];
+                        fk[c] = Fi[xk];
+                    }
+#pragma unroll
+                    for (int c = 0; c < kScanBatch; ++c) {
+                        const int x = x0 + 32 * c;
+                        if (x < P) {
+                            Uo[x] = f[c] ? ux[c] ^ uk[c] : ux[c];
+                            Fo[x] = f[c] ? fk[c] : 0;
+                        }
+                    }
+                }
+                __syncwarp();
+                uint64_t *tu = Ui; Ui = Uo; Uo = tu;
+                uint8_t *tf = Fi; Fi = Fo; Fo = tf;
+            }
+            // u is final; v[y] = Rb(y) ^ u[y - d p_b]
+            for (int x = lane; x < P; x += 32) {
+                const int xu = x - d * pb;
+                const bool in = (unsigned)xu < (unsigned)P;
+                const uint64_t ux = Ui[in ? xu : x];
+                __stcs(out + (int64_t)l1 * P + x, Ui[x]);
+                __stcs(out + (int64_t)l2 * P + x, V[x] ^ (in ? ux : 0ull));
+            }
+            __syncwarp();
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
 // sys_residual: first pass of a systematic decode. For every lost data line
 // j (image row lpos[j]) and column x: the bin of the projection dedicated to
 // the front that rebuilds x (direction pp), XOR the known lines' pixels of
@@ -1072,6 +1231,12 @@ DecKernel pick_lines_sys(int Q)
 }
 
 template <bool BATCHED>
+DecKernel pick_scan2(bool sys)
+{
+    return sys ? decode_scan2<BATCHED, true> : decode_scan2<BATCHED, false>;
+}
+
+template <bool BATCHED>
 DecKernel pick_cols(int Q)
 {
     switch (Q) {
@@ -1122,13 +1287,16 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     if (const char *e = getenv("MOJETTE_DECODE_STEADY")) a.steady = atoi(e) ? 1 : 0;
     else a.steady = 1;
     if (nitems <= 0) return 0;
-    if (sys && L.kernel != 0) return -EINVAL;
-    DecKernel fn = sys ? pick_lines_sys<BATCHED>(a.Q)
+    if (sys && L.kernel != 0 && L.kernel != 4) return -EINVAL;
+    if (L.kernel == 4 && a.Q != 2) return -EINVAL;
+    DecKernel fn = L.kernel == 4 ? pick_scan2<BATCHED>(sys)
+                 : sys ? pick_lines_sys<BATCHED>(a.Q)
                  : L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
                  : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
                                  : pick_fronts<BATCHED>(a.Q);
     if (!fn) return -EINVAL;
+    const int block = L.kernel == 4 ? 32 * L.G : 32;   // decode_scan2: one warp per stripe
     int err = 0;
     if ((err = record_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)L.smem))))
@@ -1148,7 +1316,8 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
             slots = it->second;
         } else {
             if ((err = record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))) return err;
-            if ((err = record_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32, (size_t)L.smem))))
+            if ((err = record_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block,
+                                                                                 (size_t)L.smem))))
                 return err;
             slots = std::max(per_sm, 1) * sms;
             cache[key] = slots;
@@ -1160,7 +1329,7 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
         a.gpc = (int)std::max<int64_t>(1, (nitems + slots - 1) / slots);
     int64_t grid = (nitems + a.gpc - 1) / a.gpc;
     if (a.persist) grid = std::min<int64_t>(grid, (int64_t)slots);
-    fn<<<(unsigned)grid, 32, (size_t)L.smem, st>>>(a);
+    fn<<<(unsigned)grid, block, (size_t)L.smem, st>>>(a);
     return record_cuda(cudaGetLastError());
 }
 

@@ -29,6 +29,9 @@ constexpr int kFastMaxLines = 15;
 // pair per lost line in decode_lines).
 constexpr int kSysMaxLines = 8;
 
+// decode_scan2: warps (one stripe each) per CTA.
+constexpr int kScanWarps = 4;
+
 // decode_stream stages and writes a stripe in this many chunks of columns,
 // by distance from the nearer end of each line's front.
 constexpr int kStreamChunks = 4;
@@ -73,6 +76,14 @@ struct Schedule {
     // warp read different banks at the steps of this path (plan.cpp).
     int32_t rowoff[kMaxLines] = {};
     bool phases_done = false;
+    // Two lines rebuilt (lines == 2): the closed form decode_scan2 solves,
+    // with projection scan_proj[0] (direction scan_p[0]) dedicated to line 0
+    // and scan_proj[1] (scan_p[1] > scan_p[0]) to line 1 over the whole
+    // line; the bin of pixel x of line j is stored word scan_src[j] - x.
+    bool scan2 = false;
+    int32_t scan_proj[2] = {};
+    int32_t scan_p[2] = {};
+    int64_t scan_src[2] = {};
     std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
 };
 
@@ -80,7 +91,8 @@ struct Schedule {
 // batch, else the defaults here).
 struct DecodeConfig {
     int kernel = 0;    // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
-                       // (all but decode_fronts for Q <= 8 only)
+                       // (all but decode_fronts for Q <= 8 only), 4: decode_scan2
+                       // (two lines rebuilt only; the default there)
     int gpc = 4;       // work items (groups of G stripes) per CTA
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
     int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
@@ -169,6 +181,9 @@ struct DecodeArgs {
     int Qd;                         // data lines per stripe
     int32_t lpos[kMaxLines];        // image row of each rebuilt line
     uint32_t known;                 // systematic: rows read from img
+    bool scan2;                     // two lines: the closed form is available
+    int32_t scan_p[2];
+    int64_t scan_src[2];
     int T;
     const uint32_t *steps;          // device
     uint32_t fwd;                   // operand pattern of the steady steps
@@ -194,6 +209,8 @@ struct DecGroup {
     int32_t chunk_done[kStreamChunks];
     int32_t lpos[kMaxLines];        // image row of each rebuilt line
     uint32_t known;                 // systematic: data rows read, not rebuilt
+    int32_t scan_p[2];              // decode_scan2: directions of lines 0 and 1
+    int32_t scan_src[2];            //   and their bins: pixel x at word scan_src - x
 };
 
 // One work item of a batched decode: nst (<= G) stripes of group `group`,

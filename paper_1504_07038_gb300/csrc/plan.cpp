@@ -396,6 +396,35 @@ int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
     }
     if (best < 0) return -ENOTRECOVERABLE;
     out->mask = mask;
+    out->scan2 = false;
+    if (L == 2 && !pl.trimmed) {
+        // the closed form for two lines: any two survivors with distinct
+        // directions; the widest gap p_b - p_a gives the fewest scan rounds
+        // (ties: the smaller directions)
+        int ba = -1, bb = -1;
+        for (int x = 0; x < m; ++x)
+            for (int y = 0; y < m; ++y) {
+                const int ia = surv[x], ib = surv[y];
+                if (pl.p[ia] >= pl.p[ib]) continue;
+                const int gap = pl.p[ib] - pl.p[ia];
+                const int big = std::max(std::abs(pl.p[ia]), std::abs(pl.p[ib]));
+                if (ba < 0 || gap > pl.p[bb] - pl.p[ba] ||
+                    (gap == pl.p[bb] - pl.p[ba] && big < std::max(std::abs(pl.p[ba]), std::abs(pl.p[bb])))) {
+                    ba = ia;
+                    bb = ib;
+                }
+            }
+        if (ba >= 0) {
+            out->scan2 = true;
+            const int idx[2] = {ba, bb};
+            for (int j = 0; j < 2; ++j) {
+                const int i = idx[j];
+                out->scan_proj[j] = i;
+                out->scan_p[j] = pl.p[i];
+                out->scan_src[j] = pl.off[i] + (int64_t)pos[j] * pl.p[i] - pl.bmin[i];
+            }
+        }
+    }
     if (pl.systematic) {
         uint32_t known = 0;
         for (int l = 0; l < pl.Q; ++l)

@@ -143,7 +143,7 @@ def test_batch_tune_keeps_results():
     mj.mojette_batch_tune(dec, reps=1)
     info = mj.mojette_batch_info(dec)
     for c in info["configs"]:
-        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3) and c["param"] >= 1
+        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3, 4) and c["param"] >= 1
     for t in m.d_out:
         t.fill_(0)
     mj.mojette_batch_run(dec)

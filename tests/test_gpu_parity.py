@@ -372,3 +372,34 @@ def test_bounded_wait_reports_timeout():
     proj = oracle.encode(img, p)
     assert (encode_gpu(plan, img) == proj).all()
     assert (decode_gpu(plan, proj, 0b000101) == img).all()
+
+
+TWO_LINE = [("4KB(3,2)", 256, 2, [-1, 1, 2]), ("8KB(3,2)", 512, 2, [-1, 1, 2]),
+            ("wide gaps", 40, 2, [-7, -2, 0, 3, 9]), ("|p| > P", 3, 2, [-5, 1, 4]),
+            ("one pixel", 1, 2, [-1, 2]), ("odd", 37, 2, [0, 5])]
+
+
+@pytest.mark.parametrize("kernel", ["default", "scan", "lines"])
+@pytest.mark.parametrize("name,P,Q,p", TWO_LINE)
+@pytest.mark.parametrize("S", [1, 5, 4096 + 7])
+def test_two_line_closed_form(monkeypatch, kernel, name, P, Q, p, S):
+    """Two-line images decode by decode_scan2 (the chain recurrence of the two
+    dedicated projections, evaluated by pointer doubling) unless the sweep is
+    forced: every mask leaving >= 2 projections, ragged work items (4 stripes
+    per CTA), bit-exact with the oracle."""
+    if kernel != "default":
+        monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+    n = len(p)
+    img = inputs.stripes(S, Q, P, seed=7 * P + S)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    d_proj = dev(proj)
+    out = empty((S, Q, P))
+    masks = [m for m in range(1 << n) if n - bin(m).count("1") >= Q]
+    if S > 100:
+        masks = masks[:4]
+    for m in masks:
+        out.fill_(0x33)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        torch.cuda.synchronize()
+        assert (host(out) == img).all(), (kernel, name, m)

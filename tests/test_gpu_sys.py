@@ -105,6 +105,27 @@ def test_sys_decode_every_mask(name, P, Q, p):
         assert (guard == GARBAGE).all(), m
 
 
+@pytest.mark.parametrize("name,P,Q,p", SYS_GEOMS)
+def test_sys_two_lost_lines_sweep_and_closed_form(monkeypatch, name, P, Q, p):
+    """Two lost data lines: decode_scan2 (the default) and the residual +
+    decode_lines sweep (forced) give the oracle's lines, for every pair of
+    lines and every surviving parity set."""
+    S = 67
+    plan = mj.Plan(P, Q, p, systematic=True)
+    img = inputs.stripes(S, Q, P, seed=5 * P + Q)
+    par = oracle.encode(img, p, threads=8)
+    r = len(p)
+    masks = [m for m in range(1 << (Q + r))
+             if bin(m & ((1 << Q) - 1)).count("1") == 2 and r - bin(m >> Q).count("1") >= 2]
+    masks = masks[:: max(1, len(masks) // 30)]
+    for kernel in ("scan", "lines"):
+        monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+        for m in masks:
+            got, guard = sys_decode_gpu(plan, par, m, img)
+            assert (got == img).all(), (kernel, m)
+            assert (guard == GARBAGE).all()
+
+
 @pytest.mark.parametrize("S", [1, 5, 31, 4096 + 13])
 def test_sys_decode_sizes(S):
     """One stripe, a few, one warp's worth minus one, and enough stripes for
