@@ -79,11 +79,10 @@ KERNEL_SOURCES = ["encode_kernels.cuh", "decode_kernels.cuh", "encode.cu", "deco
                   "mojette_internal.h"]
 
 
-def decode_kernel_name(Q: int) -> str:
-    """The decode kernel the library launches for Q lines (decode.cu)."""
-    if Q <= 8 and os.environ.get("MOJETTE_DECODE_KERNEL", "") != "fronts":
-        return "decode_lines"
-    return "decode_fronts"
+def decode_kernel_name(plan, mask) -> str:
+    """The decode kernel the library launches for this plan and mask."""
+    from paper_1504_07038_gb300 import binding as mj
+    return mj.mojette_decode_kernel(plan, mask)
 
 
 def workload_masks(w):
@@ -305,7 +304,7 @@ def run_gpu(args, w):
     dec_bytes = S * 2 * Q * P * 8
     peak, peak_kind = measured_peaks()
     dec_gbs = dec_bytes / (dec_ms_avg * 1e-3) / 1e9
-    dec_name = decode_kernel_name(Q)
+    dec_name = decode_kernel_name(plan, masks[0])
     # the ncu record was taken at the workload's own stripe count
     traffic_key = args.workload if not args.stripes else None
     enc_gbs = enc_bytes / (enc_ms_avg * 1e-3) / 1e9

@@ -232,6 +232,27 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
                            mojette_stream_t stream);
 
 /*
+ * mojette_decode_kernel -- which decode kernel mojette_decode (or, for a
+ * systematic plan, mojette_sys_decode) launches for this mask (host only;
+ * builds and caches the mask's path like the decode would):
+ *   0 decode_lines   the two-front path of Sec. 2.2, one lane per line and
+ *                    front (Q <= 8);
+ *   1 decode_fronts  the same path, one lane per front (any Q);
+ *   2 decode_stream, 3 decode_cols  variants of 0 (tuning candidates);
+ *   4 decode_scan2   two rebuilt lines in closed form (a chain recurrence);
+ *   5 decode_vander  every line at once: Eq. 1 as a Vandermonde system
+ *                    solved by divided differences (non-systematic,
+ *                    untrimmed plans);
+ *  -1                no launch (a systematic mask with no data line lost).
+ * The choice is the measured-fastest kernel that applies, or the one the
+ * MOJETTE_DECODE_KERNEL environment variable names (lines, fronts, stream,
+ * cols, scan, vander) where it applies; a stripe too wide for the chosen
+ * kernel's shared memory falls back to decode_lines, then decode_fronts, at
+ * launch. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
+ */
+int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int32_t *kernel);
+
+/*
  * mojette_schedule -- the cached reconstruction path for one erasure mask,
  * copied out for inspection (host only, touches no device).
  *   survivors[Q]  receives the projection index dedicated to the left-to-

@@ -56,6 +56,7 @@ def lib():
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_sys_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
+            L.mojette_decode_kernel.argtypes = [_PTR, _U32, ctypes.POINTER(ctypes.c_int32)]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_batch_create.argtypes = [_PTR, _I64, _U32, ctypes.POINTER(_PTR)]
             L.mojette_batch_update.argtypes = [_PTR, _PTR, _I64, _PTR]
@@ -78,6 +79,7 @@ def lib():
                          "mojette_plan_destroy",
                          "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc", "mojette_sys_decode",
+                         "mojette_decode_kernel",
                          "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
                          "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
                          "mojette_batch_destroy", "mojette_server_create", "mojette_server_submit",
@@ -287,6 +289,18 @@ def mojette_decode_noalloc(plan: Plan, d_proj, erasure_mask: int, d_img, S: int 
     _check(lib().mojette_decode_noalloc(plan.handle, _addr(d_proj), int(erasure_mask) & 0xFFFFFFFF,
                                         _addr(d_img), int(S), _stream(stream)),
            "mojette_decode_noalloc")
+
+
+DECODE_KERNELS = {-1: None, 0: "decode_lines", 1: "decode_fronts", 2: "decode_stream", 3: "decode_cols",
+                  4: "decode_scan2", 5: "decode_vander"}
+
+
+def mojette_decode_kernel(plan: Plan, erasure_mask: int) -> str | None:
+    """Name of the decode kernel a decode of this mask launches (None: none)."""
+    k = ctypes.c_int32()
+    _check(lib().mojette_decode_kernel(plan.handle, int(erasure_mask) & 0xFFFFFFFF, ctypes.byref(k)),
+           "mojette_decode_kernel")
+    return DECODE_KERNELS[int(k.value)]
 
 
 def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:

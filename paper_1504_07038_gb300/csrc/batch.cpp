@@ -38,6 +38,8 @@ struct Klass {
     int span = 0;                   // widest row distance between two of them
     bool sys = false;               // systematic plan: in-place decode of the lost lines
     bool scan_ok = false;           // two lines and every group has the closed form (decode_scan2)
+    bool van_ok = false;            // every group has the Vandermonde form (decode_vander)
+    int van_maxp = 0;               //   and the largest |p| its paths use
     int32_t rowoff[kMaxLines] = {};   // row phases of its largest group
     DecodeConfig dcfg;
     EncodeConfig ecfg;
@@ -111,7 +113,9 @@ int class_layout(const Klass &k, const DecodeConfig &cfg, DecodeLayout *L)
 {
     if (k.sys && cfg.kernel != 0 && cfg.kernel != 4) return -EINVAL;   // decode_lines or decode_scan2
     if (cfg.kernel == 4 && !k.scan_ok) return -EINVAL;
-    return decode_layout(k.plan->P, k.lines, k.span, k.maxp, k.maxT, cfg, k.rowoff, L);
+    if (cfg.kernel == 5 && !k.van_ok) return -EINVAL;
+    return decode_layout(k.plan->P, k.lines, k.span, cfg.kernel == 5 ? k.van_maxp : k.maxp, k.maxT, cfg,
+                         k.rowoff, L);
 }
 
 // Lost data lines of a systematic decode stripe (0 otherwise).
@@ -153,6 +157,7 @@ int launch_class(Batch &b, const Klass &k, cudaStream_t st)
     a.sys = k.sys;
     a.Qd = k.plan->Q;
     a.span = k.span;
+    a.van_maxp = k.van_maxp;
     a.maxp = k.maxp;
     a.maxT = k.maxT;
     for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = k.rowoff[l];
@@ -287,6 +292,7 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             k.lines = k.sys ? kl : k.plan->Q;
             k.gbase = (int64_t)groups.size();
             k.scan_ok = k.lines == 2;
+            k.van_ok = !k.sys && k.lines >= 2 && k.lines <= 8;
             int64_t big = 0;
             Schedule *big_sc = nullptr;
             for (int64_t g = r; g < e;) {
@@ -305,6 +311,16 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 gr.known = sc->known;
                 for (int l = 0; l < sc->lines; ++l) gr.lpos[l] = sc->lpos[l];
                 k.scan_ok = k.scan_ok && sc->scan2;
+                k.van_ok = k.van_ok && sc->vander;
+                gr.van_E0 = sc->van_E0;
+                gr.van_L = sc->van_L;
+                for (int j = 0; j < kMaxLines; ++j) {
+                    gr.van_q[j] = sc->van_q[j];
+                    gr.van_base[j] = (int32_t)sc->van_base[j];
+                    gr.van_lo[j] = sc->van_lo[j];
+                    gr.van_hi[j] = sc->van_hi[j];
+                    if (j < sc->lines) k.van_maxp = std::max(k.van_maxp, std::abs(sc->van_q[j]));
+                }
                 for (int j = 0; j < 2; ++j) {
                     gr.scan_p[j] = sc->scan_p[j];
                     gr.scan_src[j] = (int32_t)sc->scan_src[j];
@@ -334,12 +350,12 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             }
             // configuration: the plan's tuned one where it applies, else the
             // closed form for two lines, else decode_lines
-            k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : DecodeConfig();
-            if (!k.plan->tuned_dec && k.scan_ok) k.dcfg.kernel = 4;
-            if ((k.sys && k.dcfg.kernel != 0 && k.dcfg.kernel != 4) || (k.dcfg.kernel == 4 && !k.scan_ok)) {
-                k.dcfg = DecodeConfig();
-                if (k.scan_ok) k.dcfg.kernel = 4;
-            }
+            DecodeConfig def;
+            def.kernel = choose_decode_kernel(k.plan->P, k.lines, k.sys, k.scan_ok, k.van_ok, false);
+            k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : def;
+            if ((k.sys && k.dcfg.kernel != 0 && k.dcfg.kernel != 4) || (k.dcfg.kernel == 4 && !k.scan_ok) ||
+                (k.dcfg.kernel == 5 && !k.van_ok))
+                k.dcfg = def;
             if (big_sc && k.count >= kPhaseMinStripes) {
                 const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
                 for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = ph[l];
@@ -504,6 +520,8 @@ int tune(Batch &b, cudaStream_t st, int reps)
             std::vector<Cand> cands;
             if (k.scan_ok)
                 for (int g : {1, 2, 4, 8}) cands.push_back({4, g, 0, 0});
+            if (k.van_ok)
+                for (int g : {1, 2, 4, 8}) cands.push_back({5, g, 0, 0});
             if (k.sys) {
                 for (int sp : {0, 1})
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});

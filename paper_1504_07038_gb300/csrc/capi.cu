@@ -71,6 +71,15 @@ static void fill_decode_args(const Plan &pl, const Schedule &sc, int64_t S, Deco
         a->scan_p[j] = sc.scan_p[j];
         a->scan_src[j] = sc.scan_src[j];
     }
+    a->vander = sc.vander;
+    a->van_E0 = sc.van_E0;
+    a->van_L = sc.van_L;
+    for (int j = 0; j < kMaxLines; ++j) {
+        a->van_q[j] = sc.van_q[j];
+        a->van_base[j] = sc.van_base[j];
+        a->van_lo[j] = sc.van_lo[j];
+        a->van_hi[j] = sc.van_hi[j];
+    }
 }
 
 // Erasure mask bits a plan defines: n projections, or for a systematic plan
@@ -176,8 +185,9 @@ int mojette_plan_config(mojette_plan_t plan, int32_t *get, const int32_t *set)
     }
     if (set) {
         if (set[0]) {
-            if (set[1] < 0 || set[1] > 4 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
+            if (set[1] < 0 || set[1] > 5 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
                 return -EINVAL;
+            if (set[1] == 5 && (pl->systematic || pl->trimmed || pl->Q < 2)) return -EINVAL;
             if (set[1] != 1 && pl->Q > 8) return -EINVAL;
             if (set[1] == 4 && pl->Q != 2 && !pl->systematic) return -EINVAL;
             pl->dec_cfg.kernel = set[1];
@@ -330,6 +340,23 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
+}
+
+int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int32_t *kernel)
+{
+    if (!plan || !kernel) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->Q > kMaxLines) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    if (sc->lines == 0) {
+        *kernel = -1;                       // systematic, nothing lost: no launch
+        return 0;
+    }
+    *kernel = choose_decode_kernel(pl->P, sc->lines, pl->systematic, sc->scan2, sc->vander, true);
+    return 0;
 }
 
 int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *survivors,

@@ -8,6 +8,26 @@
 
 namespace mojette {
 
+int choose_decode_kernel(int P, int Q, bool sys, bool scan2, bool vander, bool env)
+{
+    int k = 0;
+    if (Q > 8) k = 1;
+    else if (sys) k = scan2 ? 4 : 0;
+    else if (vander && (Q <= 3 || (Q == 4 && P >= 192))) k = 5;
+    else if (scan2) k = 4;
+    if (env) {
+        if (const char *e = getenv("MOJETTE_DECODE_KERNEL")) {
+            if (strcmp(e, "lines") == 0 && Q <= 8) k = 0;
+            else if (strcmp(e, "fronts") == 0 && !sys) k = 1;
+            else if (strcmp(e, "stream") == 0 && !sys && Q <= 8) k = 2;
+            else if (strcmp(e, "cols") == 0 && !sys && Q <= 8) k = 3;
+            else if (strcmp(e, "scan") == 0 && scan2) k = 4;
+            else if (strcmp(e, "vander") == 0 && vander) k = 5;
+        }
+    }
+    return k;
+}
+
 int decode_bank_slots(int Q)
 {
     const int G = std::max(1, 32 / (2 * Q));
@@ -32,6 +52,21 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
     for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = L->reach + l * L->RP;
     const int want = (cfg.kernel == 1 || Q > 8) ? 1 : cfg.kernel;
     L->kernel = want;
+    if (want == 5) {
+        // decode_vander: one warp per stripe, kVanWarps per CTA; Q + 1 frame
+        // arrays of RP = P + 2 (Q - 1) maxp + 2 words (a bound on every
+        // path's frame; maxp over the directions it uses) with `reach` =
+        // maxp zero words on both sides (the largest shift)
+        if (Q < 2 || Q > 8) return -EINVAL;
+        L->G = kVanWarps;
+        L->GS = L->G;
+        L->reach = std::max(1, maxp);
+        L->RP = P + 2 * (Q - 1) * maxp + 2;
+        L->TS = 0;
+        L->SWc = (Q + 1) * (L->RP + 2 * L->reach);
+        L->smem = (int64_t)L->G * L->SWc * 8;
+        return L->smem > cap ? -EINVAL : 0;
+    }
     if (want == 4) {
         // decode_scan2: two lines, one warp per stripe, kScanWarps per CTA
         if (Q != 2) return -EINVAL;
@@ -150,18 +185,21 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         a.grp.scan_p[j] = d.scan_p[j];
         a.grp.scan_src[j] = (int32_t)d.scan_src[j];
     }
-
-    // decode_scan2 for two lines, decode_lines for Q <= 8, unless
-    // MOJETTE_DECODE_KERNEL names another
-    DecodeConfig cfg;
-    if (d.scan2) cfg.kernel = 4;
-    if (const char *kenv = getenv("MOJETTE_DECODE_KERNEL")) {
-        if (strcmp(kenv, "lines") == 0) cfg.kernel = 0;
-        else if (strcmp(kenv, "fronts") == 0) cfg.kernel = 1;
-        else if (strcmp(kenv, "stream") == 0) cfg.kernel = 2;
-        else if (strcmp(kenv, "cols") == 0) cfg.kernel = 3;
-        else if (strcmp(kenv, "scan") == 0 && d.scan2) cfg.kernel = 4;
+    int vmaxp = 0;
+    a.grp.van_E0 = d.van_E0;
+    a.grp.van_L = d.van_L;
+    for (int j = 0; j < kMaxLines; ++j) {
+        a.grp.van_q[j] = d.van_q[j];
+        a.grp.van_base[j] = (int32_t)d.van_base[j];
+        a.grp.van_lo[j] = d.van_lo[j];
+        a.grp.van_hi[j] = d.van_hi[j];
+        if (j < d.Q) vmaxp = std::max(vmaxp, std::abs(d.van_q[j]));
     }
+
+    // the measured-fastest kernel that applies, unless MOJETTE_DECODE_KERNEL
+    // names another
+    DecodeConfig cfg;
+    cfg.kernel = choose_decode_kernel(d.P, d.Q, d.sys, d.scan2, d.vander, true);
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
     if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;
@@ -171,7 +209,6 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         // which removes the known lines itself); otherwise residual bins
         // into the lost rows, then the path on them (decode_lines; no path
         // for one lost line)
-        if (cfg.kernel != 4) cfg.kernel = 0;
         const int span = d.lpos[d.Q - 1] - d.lpos[0];
         int err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
         if (err == -EINVAL && cfg.kernel == 4) {
@@ -185,8 +222,8 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         if (d.T == 0) return 0;
         return launch_decode_kernel<false>(a, L, cfg, nitems, st, true);
     }
-    int err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
-    if (err == -EINVAL && cfg.kernel == 4) {
+    int err = decode_layout(d.P, d.Q, d.Q - 1, cfg.kernel == 5 ? vmaxp : maxp, d.T, cfg, d.rowoff, &L);
+    if (err == -EINVAL && (cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 4 || cfg.kernel == 5)) {
         cfg.kernel = 0;
         err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
     }

@@ -1113,6 +1113,179 @@ __global__ void __launch_bounds__(32 * kScanWarps) decode_scan2(const __grid_con
 }
 
 // ---------------------------------------------------------------------------
+// decode_vander: every line at once, from the Vandermonde form of Eq. 1.
+// Write line l as the Laurent polynomial U_l(z) = sum_x f(x, l) z^(-x) and
+// projection i as R_i(z) = sum_b bin_b z^b; Eq. 1 with q = 1 says
+//     R_i = sum_l U_l w_i^l,   w_i = z^(p_i),
+// a Vandermonde system over GF(2)[z, 1/z] in the Q unknowns U_l, which has
+// one solution when the Q directions differ (Eq. 3). It is solved by the
+// Bjorck-Pereyra algorithm (Newton divided differences, then the Newton to
+// monomial conversion), whose only non-trivial step is a division by
+// w_i - w_j = z^(p_j) (1 + z^d), d = p_i - p_j > 0: a shift, then a prefix
+// XOR with stride d (q[e] = a[e] ^ q[e - d], exact because the quotient is
+// a polynomial). Over the Q chosen projections (ascending p):
+//   for k = 0 .. Q-2, i = Q-1 down to k+1, j = i-k-1:
+//       c_i <- (c_i ^ c_{i-1}) / (w_i - w_j)
+//   for k = Q-2 down to 0, i = k .. Q-2:
+//       c_i <- c_i ^ w_k c_{i+1}
+// and then c_l = U_l. Every polynomial lives on one frame of positions
+// [E0, E0 + L) (the bins' span plus one; no intermediate leaves it). A
+// division's prefix runs along the d chains r, r + d, r + 2d, ... of the
+// frame, each split into segments over several lanes: a pass for the
+// segments' XOR totals, a segmented shuffle scan across the lanes of a
+// chain, a pass writing the prefix with its carry. No step waits on
+// another stripe or on a ~P/2-step path: the work is ~Q^2 / 2 parallel
+// passes over the frame. One warp per stripe, kVanWarps per CTA; per warp
+// Q + 1 frame arrays in shared memory (one spare for division outputs).
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32 * kVanWarps) decode_vander(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    constexpr int JMAX = 16;            // chain-segment values kept in registers
+    const int P = a.P;
+    const int L = a.RP;                 // frame words (the same for every path of the launch)
+    const int PAD = a.reach;            // zero words on both sides of each array
+    const int AS = L + 2 * PAD;         // array stride
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *wbase = sm + (size_t)warp * a.SWc;
+    // the pads are never written: zero them once
+    for (int j = 0; j <= Q; ++j)
+        for (int t = lane; t < PAD; t += 32) {
+            wbase[(size_t)j * AS + t] = 0ull;
+            wbase[(size_t)j * AS + PAD + L + t] = 0ull;
+        }
+    uint64_t *base = wbase + PAD;
+
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + a.G - 1) / a.G;
+    for_items(a, nitems, [&](int64_t item) {
+        const DecGroup *gr;
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            gr = a.groups + wk.group;
+            nst = wk.nst;
+            first = wk.first;
+        } else {
+            gr = &a.grp;
+            s0 = item * a.G;
+            nst = (int)min64(a.G, a.S - s0);
+        }
+        if (warp < nst) {
+            const uint64_t *src = BATCHED ? a.srcp[first + warp] : a.proj + (s0 + warp) * a.total;
+            uint64_t *out = BATCHED ? a.dstp[first + warp] : a.img + (s0 + warp) * (int64_t)Q * P;
+            const int E0 = gr->van_E0;
+            int q[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) q[j] = gr->van_q[j];
+            // physical array of each c_j, and the spare one
+            int phys[Q + 1];
+#pragma unroll
+            for (int j = 0; j <= Q; ++j) phys[j] = j;
+            auto arr = [&](int j) { return base + (size_t)phys[j] * AS; };
+
+            // stage the bins: array j position e - E0 <- bin e of projection j
+            // (0 outside the projection)
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                const int lo = gr->van_lo[j] - E0, hi = gr->van_hi[j] - E0;
+                const uint64_t *sj = src + (gr->van_base[j] + E0);
+                uint64_t *c = base + (size_t)j * AS;
+                for (int t = lane; t < L; t += 32) {
+                    if (t >= lo && t < hi) cp_async8(c + t, sj + t);
+                    else c[t] = 0ull;
+                }
+            }
+            cp_async_wait_all();
+            __syncwarp();
+
+            // Newton divided differences: c_i <- (c_i ^ c_{i-1}) shifted by
+            // -q_j, divided by 1 + z^d (prefix XOR along the d chains)
+#pragma unroll
+            for (int k = 0; k < Q - 1; ++k) {
+#pragma unroll
+                for (int i = Q - 1; i > k; --i) {
+                    const int j = i - k - 1;
+                    const int d = q[i] - q[j], sh = q[j];
+                    const uint64_t *A = arr(i) + sh, *B = arr(i - 1) + sh;
+                    uint64_t *O = arr(Q);
+                    // chains r = 0 .. d-1 of the frame; cpp = 2^c >= d chains per
+                    // pass, m = 32 / cpp lanes per chain (a power of two: lane
+                    // -> (chain, segment) by mask and shift)
+                    const int c = d <= 32 ? 32 - __clz(d - 1) : 5;
+                    const int cpp = 1 << c, m = 32 >> c;
+                    const int r0 = lane & (cpp - 1), sg = lane >> c;
+                    for (int c0 = 0; c0 < d; c0 += cpp) {
+                        const int r = c0 + r0;
+                        // chain r holds positions r + d t, t < len_r
+                        const int len0 = (L - c0 + d - 1) / d;        // warp-uniform
+                        const int rem = L - c0 - (len0 - 1) * d;      // chains c0 .. c0+rem-1 have len0
+                        const int J = (len0 + m - 1) >> (5 - c);
+                        const int lenr = r < d ? (r0 < rem ? len0 : len0 - 1) : 0;
+                        const int n = max(0, min(J, lenr - sg * J));
+                        const int e0 = r + d * sg * J;
+                        uint64_t nv[JMAX];
+                        uint64_t tot = 0;
+#pragma unroll
+                        for (int t = 0; t < JMAX; ++t) {
+                            if (t >= n) break;
+                            nv[t] = A[e0 + t * d] ^ B[e0 + t * d];
+                            tot ^= nv[t];
+                        }
+                        for (int t = JMAX; t < n; ++t) {
+                            const int e = e0 + t * d;
+                            tot ^= A[e] ^ B[e];
+                        }
+                        // inclusive scan over the segments of a chain (lanes cpp apart)
+                        uint64_t inc = tot;
+                        for (int w = 1; w < m; w <<= 1) {
+                            const uint64_t o = __shfl_up_sync(0xffffffffu, inc, w << c);
+                            if (sg >= w) inc ^= o;
+                        }
+                        uint64_t v = inc ^ tot;               // carry from earlier segments
+#pragma unroll
+                        for (int t = 0; t < JMAX; ++t) {
+                            if (t >= n) break;
+                            v ^= nv[t];
+                            O[e0 + t * d] = v;
+                        }
+                        for (int t = JMAX; t < n; ++t) {
+                            const int e = e0 + t * d;
+                            v ^= A[e] ^ B[e];
+                            O[e] = v;
+                        }
+                    }
+                    __syncwarp();
+                    const int tmp = phys[i];
+                    phys[i] = phys[Q];
+                    phys[Q] = tmp;
+                }
+            }
+            // Newton form to the coefficients: c_i <- c_i ^ z^(q_k) c_{i+1}
+#pragma unroll
+            for (int k = Q - 2; k >= 0; --k) {
+#pragma unroll
+                for (int i = k; i < Q - 1; ++i) {
+                    uint64_t *C = arr(i);
+                    const uint64_t *D = arr(i + 1) - q[k];
+#pragma unroll 4
+                    for (int t = lane; t < L; t += 32) C[t] ^= D[t];
+                    __syncwarp();
+                }
+            }
+            // line l = c_l at positions -x
+#pragma unroll
+            for (int l = 0; l < Q; ++l) {
+                const uint64_t *C = arr(l) - E0;
+                for (int x = lane; x < P; x += 32) __stcs(out + (int64_t)l * P + x, C[-x]);
+            }
+            __syncwarp();
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
 // sys_residual: first pass of a systematic decode. For every lost data line
 // j (image row lpos[j]) and column x: the bin of the projection dedicated to
 // the front that rebuilds x (direction pp), XOR the known lines' pixels of
@@ -1231,6 +1404,21 @@ DecKernel pick_lines_sys(int Q)
 }
 
 template <bool BATCHED>
+DecKernel pick_vander(int Q)
+{
+    switch (Q) {
+    case 2: return decode_vander<2, BATCHED>;
+    case 3: return decode_vander<3, BATCHED>;
+    case 4: return decode_vander<4, BATCHED>;
+    case 5: return decode_vander<5, BATCHED>;
+    case 6: return decode_vander<6, BATCHED>;
+    case 7: return decode_vander<7, BATCHED>;
+    case 8: return decode_vander<8, BATCHED>;
+    default: return nullptr;
+    }
+}
+
+template <bool BATCHED>
 DecKernel pick_scan2(bool sys)
 {
     return sys ? decode_scan2<BATCHED, true> : decode_scan2<BATCHED, false>;
@@ -1289,14 +1477,15 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     if (nitems <= 0) return 0;
     if (sys && L.kernel != 0 && L.kernel != 4) return -EINVAL;
     if (L.kernel == 4 && a.Q != 2) return -EINVAL;
-    DecKernel fn = L.kernel == 4 ? pick_scan2<BATCHED>(sys)
+    DecKernel fn = L.kernel == 5 ? pick_vander<BATCHED>(a.Q)
+                 : L.kernel == 4 ? pick_scan2<BATCHED>(sys)
                  : sys ? pick_lines_sys<BATCHED>(a.Q)
                  : L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
                  : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
                                  : pick_fronts<BATCHED>(a.Q);
     if (!fn) return -EINVAL;
-    const int block = L.kernel == 4 ? 32 * L.G : 32;   // decode_scan2: one warp per stripe
+    const int block = (L.kernel == 4 || L.kernel == 5) ? 32 * L.G : 32;   // one warp per stripe
     int err = 0;
     if ((err = record_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)L.smem))))

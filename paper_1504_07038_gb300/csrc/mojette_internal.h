@@ -31,6 +31,8 @@ constexpr int kSysMaxLines = 8;
 
 // decode_scan2: warps (one stripe each) per CTA.
 constexpr int kScanWarps = 4;
+// decode_vander: warps (one stripe each) per CTA.
+constexpr int kVanWarps = 4;
 
 // decode_stream stages and writes a stripe in this many chunks of columns,
 // by distance from the nearer end of each line's front.
@@ -84,6 +86,18 @@ struct Schedule {
     int32_t scan_proj[2] = {};
     int32_t scan_p[2] = {};
     int64_t scan_src[2] = {};
+    // decode_vander (every line at once, the Vandermonde form of Eq. 1): Q
+    // survivors with ascending directions van_q, projection van_proj[j];
+    // the bin at position b of projection j is stored word van_base[j] + b
+    // for b in [van_lo[j], van_hi[j]); the solve runs over positions
+    // [van_E0, van_E0 + van_L).
+    bool vander = false;
+    int32_t van_proj[kMaxLines] = {};
+    int32_t van_q[kMaxLines] = {};
+    int64_t van_base[kMaxLines] = {};
+    int32_t van_lo[kMaxLines] = {};
+    int32_t van_hi[kMaxLines] = {};
+    int32_t van_E0 = 0, van_L = 0;
     std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
 };
 
@@ -92,7 +106,8 @@ struct Schedule {
 struct DecodeConfig {
     int kernel = 0;    // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
                        // (all but decode_fronts for Q <= 8 only), 4: decode_scan2
-                       // (two lines rebuilt only; the default there)
+                       // (two lines rebuilt only; the default there), 5: decode_vander
+                       // (non-systematic, untrimmed, 2 <= Q <= 8)
     int gpc = 4;       // work items (groups of G stripes) per CTA
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
     int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
@@ -131,6 +146,14 @@ struct Plan {
     DecodeConfig dec_cfg;
     EncodeConfig enc_cfg;
 };
+
+// Decode kernel a launch uses by default (DecodeConfig::kernel numbering),
+// before the shared-memory fit check: the measured-fastest kernel that
+// applies (decode_vander for Q <= 3, and Q = 4 with P >= 192; decode_scan2
+// for other two-line decodes; decode_lines up to 8 lines; decode_fronts
+// beyond). `env`: MOJETTE_DECODE_KERNEL may name another kernel that
+// applies.
+int choose_decode_kernel(int P, int Q, bool sys, bool scan2, bool vander, bool env);
 
 // ---- host helpers (plan.cpp) ---------------------------------------------
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);
@@ -184,6 +207,10 @@ struct DecodeArgs {
     bool scan2;                     // two lines: the closed form is available
     int32_t scan_p[2];
     int64_t scan_src[2];
+    bool vander;                    // decode_vander is available
+    int32_t van_q[kMaxLines], van_lo[kMaxLines], van_hi[kMaxLines];
+    int64_t van_base[kMaxLines];
+    int32_t van_E0, van_L;
     int T;
     const uint32_t *steps;          // device
     uint32_t fwd;                   // operand pattern of the steady steps
@@ -211,6 +238,11 @@ struct DecGroup {
     uint32_t known;                 // systematic: data rows read, not rebuilt
     int32_t scan_p[2];              // decode_scan2: directions of lines 0 and 1
     int32_t scan_src[2];            //   and their bins: pixel x at word scan_src - x
+    int32_t van_q[kMaxLines];       // decode_vander (see Schedule)
+    int32_t van_base[kMaxLines];
+    int32_t van_lo[kMaxLines];
+    int32_t van_hi[kMaxLines];
+    int32_t van_E0, van_L;
 };
 
 // One work item of a batched decode: nst (<= G) stripes of group `group`,
@@ -241,6 +273,7 @@ struct DecBatchArgs {
     int P, Q;                       // Q: lines rebuilt (systematic: lost lines)
     bool sys;                       // systematic: dstp[s] holds the Qd data lines, in place
     int Qd, span;
+    int van_maxp;                   // decode_vander: largest |p| its groups use
     int maxp, maxT;                 // over the groups (layout)
     int32_t rowoff[kMaxLines];      // decode_lines row offsets for the launch
     const DecGroup *groups;         // device

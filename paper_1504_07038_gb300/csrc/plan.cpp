@@ -425,6 +425,29 @@ int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
             }
         }
     }
+    out->vander = false;
+    if (!pl.systematic && !pl.trimmed && L >= 2 && L <= 8) {
+        // decode_vander: the first Q survivors by |p| (the narrowest frame),
+        // ascending directions
+        std::vector<int> v(surv.begin(), surv.begin() + L);
+        std::sort(v.begin(), v.end(), [&](int x, int y) { return pl.p[x] < pl.p[y]; });
+        const int64_t E0 = -(int64_t)(pl.P - 1) + std::min<int64_t>(0, (int64_t)(L - 1) * pl.p[v[0]]);
+        const int64_t top = (int64_t)(L - 1) * std::max(0, pl.p[v[L - 1]]);
+        const int64_t Lw = top - E0 + 2;
+        if (Lw < (1 << 20)) {
+            out->vander = true;
+            out->van_E0 = (int32_t)E0;
+            out->van_L = (int32_t)Lw;
+            for (int j = 0; j < L; ++j) {
+                const int i = v[j];
+                out->van_proj[j] = i;
+                out->van_q[j] = pl.p[i];
+                out->van_base[j] = pl.off[i] - pl.bmin[i];
+                out->van_lo[j] = (int32_t)pl.bmin[i];
+                out->van_hi[j] = (int32_t)(pl.bmin[i] + pl.B[i]);
+            }
+        }
+    }
     if (pl.systematic) {
         uint32_t known = 0;
         for (int l = 0; l < pl.Q; ++l)

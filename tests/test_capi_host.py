@@ -368,3 +368,29 @@ def test_sys_calls_validate_arguments_without_a_device():
     assert L.mojette_plan_ex(16, 12, nine, 9, mj.MOJETTE_PLAN_SYSTEMATIC, ctypes.byref(h)) == 0
     assert L.mojette_sys_decode(h.value, 16, (1 << 9) - 1, 16, 1, None) == -errno.EINVAL   # 9 lines lost
     L.mojette_plan_destroy(h.value)
+
+
+def test_decode_kernel_choice():
+    """The kernel a decode launches: decode_vander for Q <= 3 and 8 KB-wide
+    Q = 4 stripes, decode_lines for other Q <= 8, decode_fronts beyond,
+    decode_scan2 for systematic two-line losses, none when a systematic
+    stripe lost no data line; MOJETTE_DECODE_KERNEL overrides where the
+    kernel applies."""
+    import os
+    six = [-3, -2, -1, 1, 2, 3]
+    assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_vander"
+    assert mj.mojette_decode_kernel(mj.mojette_plan(128, 4, six), 0b11) == "decode_lines"
+    assert mj.mojette_decode_kernel(mj.mojette_plan(256, 2, [-1, 1, 2]), 0b1) == "decode_vander"
+    assert mj.mojette_decode_kernel(mj.mojette_plan(64, 8, [v for v in range(-6, 7) if v]), 0xF) == "decode_lines"
+    assert mj.mojette_decode_kernel(mj.mojette_plan(16, 9, list(range(-5, 5))), 0) == "decode_fronts"
+    sysp = mj.Plan(128, 4, [-1, 1], systematic=True)
+    assert mj.mojette_decode_kernel(sysp, 0b0110) == "decode_scan2"
+    assert mj.mojette_decode_kernel(sysp, 0b0100) == "decode_lines"
+    assert mj.mojette_decode_kernel(sysp, 0b11 << 4) is None
+    tr = mj.mojette_plan_ex(256, 4, six, mj.MOJETTE_PLAN_TRIM_UNUSED)
+    assert mj.mojette_decode_kernel(tr, 0b11) == "decode_lines"        # trimmed: no full frame
+    os.environ["MOJETTE_DECODE_KERNEL"] = "lines"
+    try:
+        assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_lines"
+    finally:
+        del os.environ["MOJETTE_DECODE_KERNEL"]

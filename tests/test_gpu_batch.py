@@ -143,7 +143,7 @@ def test_batch_tune_keeps_results():
     mj.mojette_batch_tune(dec, reps=1)
     info = mj.mojette_batch_info(dec)
     for c in info["configs"]:
-        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3, 4) and c["param"] >= 1
+        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3, 4, 5) and c["param"] >= 1
     for t in m.d_out:
         t.fill_(0)
     mj.mojette_batch_run(dec)
@@ -165,7 +165,8 @@ def test_every_tuner_candidate_is_exact(monkeypatch):
     proj = oracle.encode(img, p, threads=8)
     d_proj = torch.from_numpy(proj.view(np.int64)).cuda()
     mask = 0b000011000011
-    cases = [(k, g, r) for k in ("lines", "fronts", "stream", "cols") for g in ("1", "3", "8") for r in ("0", "1")]
+    cases = [(k, g, r) for k in ("lines", "fronts", "stream", "cols", "vander") for g in ("1", "3", "8")
+             for r in ("0", "1")]
     for kernel, gpc, rowoff in cases:
         monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
         monkeypatch.setenv("MOJETTE_DECODE_GPC", gpc)

@@ -212,7 +212,7 @@ def test_full_size_wide_geometry():
 
 
 VARIANTS = [("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts", {}), ("stream", {}),
-            ("cols", {})]
+            ("cols", {}), ("vander", {}), ("vander", {"MOJETTE_DECODE_GPC": "1"})]
 
 
 @pytest.mark.parametrize("kernel,K", VARIANTS)
@@ -221,8 +221,8 @@ VARIANTS = [("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts",
                             ("odd P(8,6)", 33, 6, [-4, -3, -1, 1, 2, 3, 5, 7])])
 def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
     """Each decode kernel (decode_lines with and without row phases,
-    decode_fronts, decode_stream, decode_cols), every k-of-n mask (sampled
-    at (12,8)), bit-exact."""
+    decode_fronts, decode_stream, decode_cols, decode_vander), every k-of-n
+    mask (sampled at (12,8)), bit-exact."""
     monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
     for k, v in K.items():
         monkeypatch.setenv(k, v)
@@ -403,3 +403,30 @@ def test_two_line_closed_form(monkeypatch, kernel, name, P, Q, p, S):
         mj.mojette_decode(plan, d_proj, m, out, S)
         torch.cuda.synchronize()
         assert (host(out) == img).all(), (kernel, name, m)
+
+
+VANDER_GEOMS = [("8KB(6,4)", 256, 4, SIX), ("4KB(12,8)", 64, 8, TWELVE), ("8KB(12,8)", 128, 8, TWELVE),
+                ("tiny", 1, 3, [-2, 0, 5, 7]), ("|p| > P", 5, 4, [-7, -1, 3, 8, 9]),
+                ("one-signed", 40, 5, [1, 2, 4, 5, 9, 11]), ("Q=2", 77, 2, [-3, 4, 6])]
+
+
+@pytest.mark.parametrize("name,P,Q,p", VANDER_GEOMS)
+@pytest.mark.parametrize("S", [1, 6, 4099])
+def test_vandermonde_decode(monkeypatch, name, P, Q, p, S):
+    """decode_vander (the Bjorck-Pereyra solve of Eq. 1's Vandermonde
+    system) on every k-of-n mask (sampled at (12,8), four masks at the
+    largest S), ragged work items, bit-exact."""
+    monkeypatch.setenv("MOJETTE_DECODE_KERNEL", "vander")
+    n = len(p)
+    img = inputs.stripes(S, Q, P, seed=11 * P + Q + S)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    d_proj = dev(proj)
+    out = empty((S, Q, P))
+    masks = [m for m in range(1 << n) if n - bin(m).count("1") >= Q]
+    masks = masks[:: max(1, len(masks) // 40)] if S < 100 else masks[:4]
+    for m in masks:
+        out.fill_(0x55)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        torch.cuda.synchronize()
+        assert (host(out) == img).all(), (name, m)
