@@ -1262,9 +1262,10 @@ __global__ void __launch_bounds__(32 * kVanWarps) decode_vander(const __grid_con
                     phys[Q] = tmp;
                 }
             }
-            // Newton form to the coefficients: c_i <- c_i ^ z^(q_k) c_{i+1}
+            // Newton form to the coefficients: c_i <- c_i ^ z^(q_k) c_{i+1};
+            // the last level (k = 0) goes straight to the output
 #pragma unroll
-            for (int k = Q - 2; k >= 0; --k) {
+            for (int k = Q - 2; k >= 1; --k) {
 #pragma unroll
                 for (int i = k; i < Q - 1; ++i) {
                     uint64_t *C = arr(i);
@@ -1274,11 +1275,16 @@ __global__ void __launch_bounds__(32 * kVanWarps) decode_vander(const __grid_con
                     __syncwarp();
                 }
             }
-            // line l = c_l at positions -x
+            // line l = c_l ^ z^(q_0) c_{l+1} (c_{Q-1} as it is) at positions -x
 #pragma unroll
             for (int l = 0; l < Q; ++l) {
                 const uint64_t *C = arr(l) - E0;
-                for (int x = lane; x < P; x += 32) __stcs(out + (int64_t)l * P + x, C[-x]);
+                if (l + 1 < Q) {
+                    const uint64_t *D = arr(l + 1) - E0 - q[0];
+                    for (int x = lane; x < P; x += 32) __stcs(out + (int64_t)l * P + x, C[-x] ^ D[-x]);
+                } else {
+                    for (int x = lane; x < P; x += 32) __stcs(out + (int64_t)l * P + x, C[-x]);
+                }
             }
             __syncwarp();
         }
