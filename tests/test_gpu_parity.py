@@ -246,7 +246,9 @@ def test_decode_time_flat_across_masks():
     """Sec. 4 (Fig. 2-3): decode cost does not depend on which projections
     are lost. Every two-erasure mask of 8 KB (6,4) on 65536 stripes, timed
     with CUDA events (median of 3): the slowest mask within 1.3x of the
-    fastest (the paths differ by at most a few steps)."""
+    fastest (decode_vander, the default here, runs the same passes for
+    every survivor set, only with other strides; the paths of decode_lines
+    differ by at most a few steps)."""
     P, Q, p, S = 256, 4, [-3, -2, -1, 1, 2, 3], 65536
     plan = mj.mojette_plan(P, Q, p)
     img = torch.from_numpy(inputs.stripes(S, Q, P, seed=3).view(np.int64)).cuda()
