@@ -79,10 +79,10 @@ KERNEL_SOURCES = ["encode_kernels.cuh", "decode_kernels.cuh", "encode.cu", "deco
                   "mojette_internal.h"]
 
 
-def decode_kernel_name(plan, mask) -> str:
-    """The decode kernel the library launches for this plan and mask."""
+def decode_kernel_name(plan, mask, S) -> str:
+    """The decode kernel the library launches for this plan, mask and size."""
     from paper_1504_07038_gb300 import binding as mj
-    return mj.mojette_decode_kernel(plan, mask)
+    return mj.mojette_decode_kernel(plan, mask, S)
 
 
 def workload_masks(w):
@@ -304,7 +304,7 @@ def run_gpu(args, w):
     dec_bytes = S * 2 * Q * P * 8
     peak, peak_kind = measured_peaks()
     dec_gbs = dec_bytes / (dec_ms_avg * 1e-3) / 1e9
-    dec_name = decode_kernel_name(plan, masks[0])
+    dec_name = decode_kernel_name(plan, masks[0], S)
     # the ncu record was taken at the workload's own stripe count
     traffic_key = args.workload if not args.stripes else None
     enc_gbs = enc_bytes / (enc_ms_avg * 1e-3) / 1e9

@@ -233,8 +233,8 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
 
 /*
  * mojette_decode_kernel -- which decode kernel mojette_decode (or, for a
- * systematic plan, mojette_sys_decode) launches for this mask (host only;
- * builds and caches the mask's path like the decode would):
+ * systematic plan, mojette_sys_decode) launches for this mask and S stripes
+ * (host only; builds and caches the mask's path like the decode would):
  *   0 decode_lines   the two-front path of Sec. 2.2, one lane per line and
  *                    front (Q <= 8);
  *   1 decode_fronts  the same path, one lane per front (any Q);
@@ -244,13 +244,15 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
  *                    solved by divided differences (non-systematic,
  *                    untrimmed plans);
  *  -1                no launch (a systematic mask with no data line lost).
- * The choice is the measured-fastest kernel that applies, or the one the
+ * The choice is the measured-fastest kernel that applies (it depends on Q,
+ * P and, for Q = 4 and 5, on whether S is at most 4096), or the one the
  * MOJETTE_DECODE_KERNEL environment variable names (lines, fronts, stream,
  * cols, scan, vander) where it applies; a stripe too wide for the chosen
  * kernel's shared memory falls back to decode_lines, then decode_fronts, at
  * launch. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
  */
-int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int32_t *kernel);
+int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int64_t S,
+                          int32_t *kernel);
 
 /*
  * mojette_schedule -- the cached reconstruction path for one erasure mask,

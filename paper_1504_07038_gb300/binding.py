@@ -56,7 +56,7 @@ def lib():
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_sys_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
-            L.mojette_decode_kernel.argtypes = [_PTR, _U32, ctypes.POINTER(ctypes.c_int32)]
+            L.mojette_decode_kernel.argtypes = [_PTR, _U32, _I64, ctypes.POINTER(ctypes.c_int32)]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_batch_create.argtypes = [_PTR, _I64, _U32, ctypes.POINTER(_PTR)]
             L.mojette_batch_update.argtypes = [_PTR, _PTR, _I64, _PTR]
@@ -295,10 +295,11 @@ DECODE_KERNELS = {-1: None, 0: "decode_lines", 1: "decode_fronts", 2: "decode_st
                   4: "decode_scan2", 5: "decode_vander"}
 
 
-def mojette_decode_kernel(plan: Plan, erasure_mask: int) -> str | None:
-    """Name of the decode kernel a decode of this mask launches (None: none)."""
+def mojette_decode_kernel(plan: Plan, erasure_mask: int, S: int = 1 << 20) -> str | None:
+    """Name of the decode kernel a decode of this mask over S stripes
+    launches (None: none)."""
     k = ctypes.c_int32()
-    _check(lib().mojette_decode_kernel(plan.handle, int(erasure_mask) & 0xFFFFFFFF, ctypes.byref(k)),
+    _check(lib().mojette_decode_kernel(plan.handle, int(erasure_mask) & 0xFFFFFFFF, int(S), ctypes.byref(k)),
            "mojette_decode_kernel")
     return DECODE_KERNELS[int(k.value)]
 

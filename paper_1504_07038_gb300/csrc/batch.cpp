@@ -351,7 +351,7 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             // configuration: the plan's tuned one where it applies, else the
             // closed form for two lines, else decode_lines
             DecodeConfig def;
-            def.kernel = choose_decode_kernel(k.plan->P, k.lines, k.sys, k.scan_ok, k.van_ok, false);
+            def.kernel = choose_decode_kernel(k.plan->P, k.lines, k.count, k.sys, k.scan_ok, k.van_ok, false);
             k.dcfg = k.plan->tuned_dec ? k.plan->dec_cfg : def;
             if ((k.sys && k.dcfg.kernel != 0 && k.dcfg.kernel != 4) || (k.dcfg.kernel == 4 && !k.scan_ok) ||
                 (k.dcfg.kernel == 5 && !k.van_ok))

@@ -342,9 +342,9 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
     return launch_decode(a, (cudaStream_t)stream);
 }
 
-int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int32_t *kernel)
+int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int64_t S, int32_t *kernel)
 {
-    if (!plan || !kernel) return -EINVAL;
+    if (!plan || !kernel || S < 0) return -EINVAL;
     Plan *pl = reinterpret_cast<Plan *>(plan);
     if (pl->Q > kMaxLines) return -EINVAL;
     if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
@@ -355,7 +355,7 @@ int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int32_t *k
         *kernel = -1;                       // systematic, nothing lost: no launch
         return 0;
     }
-    *kernel = choose_decode_kernel(pl->P, sc->lines, pl->systematic, sc->scan2, sc->vander, true);
+    *kernel = choose_decode_kernel(pl->P, sc->lines, S, pl->systematic, sc->scan2, sc->vander, true);
     return 0;
 }
 

@@ -8,12 +8,13 @@
 
 namespace mojette {
 
-int choose_decode_kernel(int P, int Q, bool sys, bool scan2, bool vander, bool env)
+int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool vander, bool env)
 {
     int k = 0;
+    const bool small = S <= kVanSmallLaunch;
     if (Q > 8) k = 1;
     else if (sys) k = scan2 ? 4 : 0;
-    else if (vander && (Q <= 3 || (Q == 4 && P >= 192))) k = 5;
+    else if (vander && (Q <= 3 || (Q == 4 && (P >= 192 || small)) || (Q == 5 && small))) k = 5;
     else if (scan2) k = 4;
     if (env) {
         if (const char *e = getenv("MOJETTE_DECODE_KERNEL")) {
@@ -199,7 +200,7 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     // the measured-fastest kernel that applies, unless MOJETTE_DECODE_KERNEL
     // names another
     DecodeConfig cfg;
-    cfg.kernel = choose_decode_kernel(d.P, d.Q, d.sys, d.scan2, d.vander, true);
+    cfg.kernel = choose_decode_kernel(d.P, d.Q, d.S, d.sys, d.scan2, d.vander, true);
     if (const char *e = getenv("MOJETTE_DECODE_GPC")) cfg.gpc = std::max(1, atoi(e));
     if (const char *e = getenv("MOJETTE_DECODE_ROWOFF")) cfg.rowoff = atoi(e) ? 1 : 0;
     if (const char *e = getenv("MOJETTE_DECODE_PERSIST")) cfg.persist = atoi(e) ? 1 : 0;

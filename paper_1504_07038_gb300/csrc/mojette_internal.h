@@ -147,13 +147,15 @@ struct Plan {
     EncodeConfig enc_cfg;
 };
 
-// Decode kernel a launch uses by default (DecodeConfig::kernel numbering),
-// before the shared-memory fit check: the measured-fastest kernel that
-// applies (decode_vander for Q <= 3, and Q = 4 with P >= 192; decode_scan2
-// for other two-line decodes; decode_lines up to 8 lines; decode_fronts
-// beyond). `env`: MOJETTE_DECODE_KERNEL may name another kernel that
-// applies.
-int choose_decode_kernel(int P, int Q, bool sys, bool scan2, bool vander, bool env);
+// Decode kernel a launch of S stripes uses by default (DecodeConfig::kernel
+// numbering), before the shared-memory fit check: the measured-fastest
+// kernel that applies (decode_vander for Q <= 3, Q = 4 with P >= 192, and
+// Q = 4 or 5 in launches of at most kVanSmallLaunch stripes, where its
+// shorter per-stripe latency wins; decode_scan2 for other two-line decodes;
+// decode_lines up to 8 lines; decode_fronts beyond). `env`:
+// MOJETTE_DECODE_KERNEL may name another kernel that applies.
+constexpr int64_t kVanSmallLaunch = 4096;
+int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool vander, bool env);
 
 // ---- host helpers (plan.cpp) ---------------------------------------------
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);

@@ -371,8 +371,9 @@ def test_sys_calls_validate_arguments_without_a_device():
 
 
 def test_decode_kernel_choice():
-    """The kernel a decode launches: decode_vander for Q <= 3 and 8 KB-wide
-    Q = 4 stripes, decode_lines for other Q <= 8, decode_fronts beyond,
+    """The kernel a decode launches: decode_vander for Q <= 3, 8 KB-wide
+    Q = 4 stripes and small Q = 4 launches, decode_lines for other Q <= 8,
+    decode_fronts beyond,
     decode_scan2 for systematic two-line losses, none when a systematic
     stripe lost no data line; MOJETTE_DECODE_KERNEL overrides where the
     kernel applies."""
@@ -380,6 +381,7 @@ def test_decode_kernel_choice():
     six = [-3, -2, -1, 1, 2, 3]
     assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_vander"
     assert mj.mojette_decode_kernel(mj.mojette_plan(128, 4, six), 0b11) == "decode_lines"
+    assert mj.mojette_decode_kernel(mj.mojette_plan(128, 4, six), 0b11, S=1024) == "decode_vander"   # small launch
     assert mj.mojette_decode_kernel(mj.mojette_plan(256, 2, [-1, 1, 2]), 0b1) == "decode_vander"
     assert mj.mojette_decode_kernel(mj.mojette_plan(64, 8, [v for v in range(-6, 7) if v]), 0xF) == "decode_lines"
     assert mj.mojette_decode_kernel(mj.mojette_plan(16, 9, list(range(-5, 5))), 0) == "decode_fronts"
