@@ -295,6 +295,7 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             k.van_ok = !k.sys && k.lines >= 2 && k.lines <= 8;
             int64_t big = 0;
             Schedule *big_sc = nullptr;
+            int64_t big_grp = -1;
             for (int64_t g = r; g < e;) {
                 const uint32_t mask = stripes[idx[g]].erasure_mask;
                 int64_t h = g;
@@ -332,6 +333,8 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                     gr.src[2 * l] = (int32_t)sc->srcL[l];
                     gr.src[2 * l + 1] = (int32_t)sc->srcR[l];
                     gr.split[l] = sc->split[l];
+                    gr.order[2 * l] = kIdentityOrder;
+                    gr.order[2 * l + 1] = kIdentityOrder;
                     gr.chunk_w = sc->chunk_w;
                     for (int c = 0; c < kStreamChunks; ++c) {
                         gr.chunk_wait[c] = sc->chunk_wait[c];
@@ -343,6 +346,7 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 if (h - g > big) {   // the largest group sets the class's row phases
                     big = h - g;
                     big_sc = sc;
+                    big_grp = (int64_t)groups.size();
                 }
                 groups.push_back(gr);
                 k.gcount.push_back(h - g);
@@ -356,9 +360,17 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
             if ((k.sys && k.dcfg.kernel != 0 && k.dcfg.kernel != 4) || (k.dcfg.kernel == 4 && !k.scan_ok) ||
                 (k.dcfg.kernel == 5 && !k.van_ok))
                 k.dcfg = def;
+            if (big_sc)   // bulk-staging parity of the largest group's rows
+                for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = big_sc->rowpar[l];
             if (big_sc && k.count >= kPhaseMinStripes) {
                 const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
                 for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = ph[l];
+                // its load orders go with those phases; the other groups
+                // keep the plain order
+                for (int l = 0; l < big_sc->lines; ++l) {
+                    groups[(size_t)big_grp].order[2 * l] = big_sc->order[2 * l];
+                    groups[(size_t)big_grp].order[2 * l + 1] = big_sc->order[2 * l + 1];
+                }
             }
             // room for the smallest G any configuration uses (1 stripe per item)
             k.wcap = k.count;

@@ -281,7 +281,8 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     a.img = d_img;
     a.steps = dsteps;
     const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
-    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : sc->rowpar[l];
+    for (int f = 0; f < 2 * kMaxLines; ++f) a.order[f] = ph ? sc->order[f] : kIdentityOrder;
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
@@ -308,7 +309,8 @@ int mojette_sys_decode(mojette_plan_t plan, const uint64_t *d_parity, uint32_t e
     a.img = d_data;
     a.steps = dsteps;
     const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
-    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : sc->rowpar[l];
+    for (int f = 0; f < 2 * kMaxLines; ++f) a.order[f] = ph ? sc->order[f] : kIdentityOrder;
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
@@ -336,7 +338,8 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj, uint32_t
     a.img = d_img;
     a.steps = dsteps;
     const int32_t *ph = S >= kPhaseMinStripes ? schedule_row_phases(*pl, *sc) : nullptr;
-    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : 0;
+    for (int l = 0; l < kMaxLines; ++l) a.rowoff[l] = ph ? ph[l] : sc->rowpar[l];
+    for (int f = 0; f < 2 * kMaxLines; ++f) a.order[f] = ph ? sc->order[f] : kIdentityOrder;
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);

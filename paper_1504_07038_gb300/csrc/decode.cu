@@ -119,7 +119,14 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
             }
         }
         L->SWc = Q * L->RP + L->reach;
-        L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
+        // the non-systematic kernel gives each stripe a region of SWr words,
+        // SWr = S mod 16 (stripe g's words g S bank slots further on; even:
+        // 16-byte aligned regions); the staging mbarrier sits after the step
+        // tables (16 bytes)
+        L->SWr = L->SWc + 1;
+        const int want_mod = (S > 1) ? S : 2;
+        while (L->SWr % 16 != want_mod % 16 || L->SWr % 2) ++L->SWr;
+        L->smem = (int64_t)L->TS * 8 + 16 + (int64_t)L->G * std::max(L->SWr, L->SWc) * 8;
         return L->smem > cap ? -EINVAL : 0;   // one warp's stripes exceed shared memory
     }
     L->SWc = Q * L->RP + L->reach;
@@ -164,6 +171,7 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
     a.Q = d.Q;
     a.Qd = d.Qd;
     a.grp.known = d.known;
+    a.status = d.status;
     for (int l = 0; l < kMaxLines; ++l) a.grp.lpos[l] = d.lpos[l];
     a.grp.steps = d.steps;
     a.grp.T = d.T;
@@ -175,6 +183,8 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         a.grp.src[2 * l] = (int32_t)d.srcL[l];
         a.grp.src[2 * l + 1] = (int32_t)d.srcR[l];
         a.grp.split[l] = d.split[l];
+        a.grp.order[2 * l] = d.order[2 * l];
+        a.grp.order[2 * l + 1] = d.order[2 * l + 1];
         maxp = std::max(maxp, std::max(std::abs(d.pL[l]), std::abs(d.pR[l])));
     }
     a.grp.chunk_w = d.chunk_w;

@@ -21,6 +21,7 @@ int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaSt
     a.P = b.P;
     a.Q = b.Q;
     a.Qd = b.Qd;
+    a.status = b.status;
     if (b.sys && L.kernel != 4) {
         // residual bins into the lost rows, then the path (none for one lost
         // line); decode_scan2 removes the known lines itself

@@ -64,6 +64,7 @@ struct DecParams {
     int reach;    // zero columns before, between and after the rows of a stripe
     int RP;       // row pitch in columns: P + reach (+ room for row phases)
     int SWc;      // columns per stripe slot
+    int SWr;      // decode_lines (not systematic): words per stripe region
     int rowbase[kMaxLines];   // decode_lines: first column of each line's row
     int G;        // stripes per work item (one warp)
     int GS;       // interleave stride (decode_lines: G; decode_fronts: G rounded to odd)
@@ -71,6 +72,7 @@ struct DecParams {
     int gpc;      // work items per CTA (one warp per CTA)
     int persist;  // 1: grid-stride over chunks of gpc items
     int steady;   // decode_fronts: 1 to run steady steps on the short path
+    uint32_t *status;   // device status word (bounded waits that time out)
 };
 
 __device__ __forceinline__ uint64_t ld_s64(uint32_t addr)
@@ -346,37 +348,63 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     constexpr int Q = QT;
     const int P = a.P, G = a.G;
     const int lane = threadIdx.x & 31;
-    // step words, forward words (TS words each), then the slots
+    // step words, forward words (TS words each), the staging mbarrier, then
+    // the slots
     uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
     uint32_t *fwdw = stepw + a.TS;
-    uint64_t *wbuf = sm + a.TS;
+    uint64_t *mbar = sm + a.TS;
+    uint64_t *wbuf = sm + a.TS + 2;
     // Zero the stripe slots once: rows are always staged before they are
     // read and the columns around them (pixels outside the image, the XOR
     // identity) are never written.
-    for (int i = lane; i < a.SWc * G; i += 32) wbuf[i] = 0;
+    const int slot_words = SYS ? a.SWc * G : a.SWr * G;
+    for (int i = lane; i < slot_words; i += 32) wbuf[i] = 0;
     const uint32_t wbase = smem_addr(wbuf);
+    const uint32_t bar = smem_addr(mbar);
+    if (!SYS && lane == 0) {
+        mbar_init(bar, 32);   // every lane arrives once per item
+        mbar_init_fence();
+    }
 
-    // Rebuild lanes: lane = (2l + side) * G + g; lanes past 2Q*G shadow lane 0.
-    const int lsr = lane / G;
-    const bool ok = lsr < 2 * Q;
-    const int ls = ok ? lsr : 0;
-    const int g = ok ? lane - lsr * G : 0;
-    const int l = ls >> 1, side = ls & 1;
-    const uint32_t bitmask = ok ? 1u << ls : 0u;   // shadow lanes never store
+    // Rebuild lanes: lane = side * 16 + l * G + g -- the left fronts in the
+    // lower half-warp, the right fronts in the upper one (a 64-bit shared
+    // load is served per half-warp, and fronts moving the same way keep
+    // their relative bank slots); lanes past Q*G in a half shadow line 0 of
+    // their side, load nothing and never store.
+    const int hl = lane & 15, lq = hl / G;
+    const bool ok = lq < Q;
+    const int l = ok ? lq : 0, side = lane >> 4;
+    const int g = ok ? hl - lq * G : 0;
+    const int ls = 2 * l + side;   // front index in the step words
+    const uint32_t bitmask = ok ? 1u << ls : 0u;
     const int myrow = a.rowbase[l];
-    const uint32_t start = wbase + ((myrow + (side ? P - 1 : 0)) * G + g) * 8;
-    const int stepb = (side ? -1 : 1) * G * 8;
-    const uint32_t has_next = (l + 1 < Q) ? 1u : 0u;
+    // Layouts. SYS: the G stripes interleaved word by word (word of column
+    // c of stripe g at (row + c) * G + g), rows in pixel order. Otherwise
+    // each stripe has its own region of SWr words (SWr = S mod 16, so the
+    // regions sit in different bank slots) with its rows in bin order --
+    // pixel x of line l at rowbase[l] + P - 1 - x -- the order of the
+    // dedicated projection's bins, so that a front's run of bins is staged
+    // by one bulk copy.
+    const uint32_t start = SYS ? wbase + ((myrow + (side ? P - 1 : 0)) * G + g) * 8
+                               : wbase + (g * a.SWr + myrow + (side ? 0 : P - 1)) * 8;
+    const int stepb = SYS ? (side ? -1 : 1) * G * 8 : (side ? 8 : -8);
 
-    // Path-dependent state. The operands of line l sit on lines
-    // l2 = l+1+k (mod Q), k = 0 .. Q-2. k = 0 is line l+1, which may be
-    // forwarded, except for l = Q-1 where it wraps to line 0 and is always
-    // read. For steady steps: this lane's link (line l forwards from line
-    // l+1) and the link state after each scan round, from the path's steady
-    // pattern: after the round with stride d, line l is still linked iff it
-    // was, and line l+d was too.
-    int T4 = 0, d0 = 0;
-    int dk[Q > 2 ? Q - 2 : 1];
+    // Path-dependent state. A front reads Q words per step: its own bin
+    // (first) and the pixels of the bin line on lines l + j (mod Q), j = 1 ..
+    // Q-1; j = 1 is line l+1, which may be rebuilt by its front in this same
+    // step (forwarded), except for l = Q-1 where it wraps to line 0.
+    // offk[k]: byte offset of the word operand load k reads, k = 0 .. Q-2 (the
+    // path's load order, chosen with the row phases so that each load
+    // instruction meets distinct bank slots). A forwarded word is read all
+    // the same: it still holds line l+1's bin, which line l+1 reads as its
+    // own, so the chain runs over b = pixel ^ own bin -- b_l = (XOR of l's
+    // operand words) ^ b_{l+1} while linked, pixel_l = b_l ^ own bin_l --
+    // and the stale bin cancels. For steady steps: this lane's link (line l
+    // forwards from line l+1) and the link state after each scan round,
+    // from the path's steady pattern: after the round with stride d, line l
+    // is still linked iff it was, and line l+d was too.
+    int T4 = 0;
+    int offk[Q > 1 ? Q - 1 : 1];
     uint32_t sfw = 0u;
     uint32_t slink[4] = {0u, 0u, 0u, 0u};
     int chain = 0;   // steady steps: lines l+1 .. l+chain are linked to this one
@@ -390,12 +418,12 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
         const int p = gr.p[ls];
         auto off = [&](int l2) {
-            const int dl = SYS ? gr.lpos[l2] - gr.lpos[l] : l2 - l;
-            return (a.rowbase[l2] - myrow + dl * p) * G * 8;
+            if constexpr (SYS) return (a.rowbase[l2] - myrow + (gr.lpos[l2] - gr.lpos[l]) * p) * G * 8;
+            else return (a.rowbase[l2] - myrow - (l2 - l) * p) * 8;
         };
-        d0 = off(has_next ? l + 1 : 0);
+        const uint32_t ord = gr.order[ls];   // nibble 0 is the own bin
 #pragma unroll
-        for (int k = 1; k < Q - 1; ++k) dk[k - 1] = off((l + 1 + k) % Q);
+        for (int k = 1; k < Q; ++k) offk[k - 1] = off((l + ((ord >> (4 * k)) & 15u)) % Q);
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
         chain = 0;
         if (ok)
@@ -428,8 +456,11 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     const bool copy_ok = xk < XK;
 
     int cur = -1;
+    uint32_t phase = 0;
+    bool dead = false;   // a staging wait timed out: stop
     const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
     for_items(a, nitems, [&](int64_t item) {
+        if (dead) return;
         int nst;
         int64_t s0 = 0, first = 0;
         if constexpr (BATCHED) {
@@ -448,28 +479,77 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             nst = (int)min64(G, a.S - s0);
         }
 
-        if (copy_ok && gg < nst) {
-            if constexpr (SYS) {
-                // the residual bins, in pixel order, in the lost rows
+        if constexpr (SYS) {
+            // the residual bins, in pixel order, in the lost rows
+            if (copy_ok && gg < nst) {
                 const uint64_t *dat = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
                 for (int ll = 0; ll < Q; ++ll) {
                     const uint64_t *srow = dat + (int64_t)grp().lpos[ll] * P;
                     uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
                     for (int x = xk; x < P; x += XK) cp_async8(dst + x * G, srow + x);
                 }
-            } else {
-                const uint64_t *src = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
-                for (int ll = 0; ll < Q; ++ll) {
-                    const int sp = grp().split[ll];
-                    const int sl = grp().src[2 * ll], sr = grp().src[2 * ll + 1];
-                    uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
-                    for (int x = xk; x < P; x += XK)
-                        cp_async8(dst + x * G, src + ((x < sp ? sl : sr) - x));
+            }
+            cp_async_wait_all();
+            __syncwarp();
+        } else {
+            // Each lane stages its own front's run of bins: n consecutive
+            // words of its dedicated projection (bins src - x for the pixels
+            // x the front rebuilds), in bin order, which is the row order.
+            // Where the run and its place in shared memory agree mod 16
+            // bytes, one bulk copy takes the aligned middle and 8-byte
+            // cp.async the odd word at either end; the other runs are copied
+            // by the whole warp, word by word. The previous item's reads and
+            // writes of the slots are ordered before the bulk writes first.
+            fence_proxy_async_smem();
+            __syncwarp();
+            int n = 0;
+            const uint64_t *gsrc = nullptr;
+            uint32_t sdst = 0;
+            if (ok && g < nst) {
+                const uint64_t *sb = BATCHED ? a.srcp[first + g] : a.proj + (s0 + g) * a.total;
+                const int sp = grp().split[l];
+                if (side == 0) {
+                    n = sp;
+                    gsrc = sb + (grp().src[2 * l] - (sp - 1));
+                    sdst = wbase + (g * a.SWr + myrow + P - sp) * 8;
+                } else {
+                    n = P - sp;
+                    gsrc = sb + (grp().src[2 * l + 1] - (P - 1));
+                    sdst = wbase + (g * a.SWr + myrow) * 8;
                 }
             }
+            const bool same = n > 0 && ((((uint32_t)(uintptr_t)gsrc) ^ sdst) & 8u) == 0;
+            const int head = same && ((uintptr_t)gsrc & 8u) ? 1 : 0;
+            const int body = same ? ((n - head) & ~1) : 0;
+            mbar_arrive_expect_tx(bar, (uint32_t)body * 8u);
+            if (body > 0) tma_load_1d(sdst + head * 8u, gsrc + head, (uint32_t)body * 8u, bar);
+            if (same) {
+                if (head) cp_async8_s(sdst, gsrc);
+                if (n - head - body) cp_async8_s(sdst + (uint32_t)(n - 1) * 8u, gsrc + (n - 1));
+            }
+            uint32_t rest = __ballot_sync(0xffffffffu, n > 0 && !same);
+            while (rest) {
+                const int src_lane = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const int nn = __shfl_sync(0xffffffffu, n, src_lane);
+                const uint64_t *gs = reinterpret_cast<const uint64_t *>(
+                    __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)gsrc, src_lane));
+                const uint32_t sd = __shfl_sync(0xffffffffu, sdst, src_lane);
+                for (int i = lane; i < nn; i += 32) cp_async8_s(sd + (uint32_t)i * 8u, gs + i);
+            }
+            cp_async_wait_all();
+            const bool arrived = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__any_sync(0xffffffffu, !arrived)) {
+                // the bulk copies did not land in time: report, let any
+                // still in flight finish (bounded) and stop
+                if (lane == 0) atomicOr(a.status, kStatusWaitTimeout);
+                mbar_wait_bounded(bar, phase ^ 1u);
+                dead = true;
+                return;
+            }
+            __syncwarp();
         }
-        cp_async_wait_all();
-        __syncwarp();
 
         uint32_t pos = start;
         // the next step's words are read one step ahead (the tables hold
@@ -481,49 +561,53 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             f_next = fwdw[t + 1];
             if (w & kStepSteady) {
                 // steady: every line moves, links are the path's pattern
-                uint64_t v = ld_s64(pos);
+                const uint64_t own = ld_s64(pos);
+                uint64_t v = 0;
 #pragma unroll
-                for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
-                if (Q > 1) v ^= ld_s64_if(pos + d0, (sfw & has_next) ^ 1u);
+                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(pos + offk[k]);
                 if constexpr (Q <= 4) {
                     // the linked lines' own values, all fetched at once: one
                     // shuffle latency instead of log2 Q dependent rounds
                     const uint64_t x = v;
 #pragma unroll
                     for (int d = 1; d < Q; ++d) {
-                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x, 2 * d * G);
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x, d * G);
                         if (d <= chain) v ^= tv;
                     }
                 } else {
 #pragma unroll
                     for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
-                        const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
                         if (slink[r]) v ^= tv;
                     }
                 }
-                st_s64_if(pos, v, ok);
+                st_s64_if(pos, v ^ own, ok);
                 pos += stepb;
                 __syncwarp();
                 continue;
             }
+            // a front that does not move this step loads nothing (its value
+            // is not used: a link always points at a front that moves)
             const uint32_t act = w & bitmask;
             const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
-            uint64_t v = ld_s64(pos);
+            uint64_t own = 0, v = 0;
+            if (act) {
+                own = ld_s64(pos);
 #pragma unroll
-            for (int k2 = 0; k2 < Q - 2; ++k2) v ^= ld_s64(pos + dk[k2]);
-            if (Q > 1) v ^= ld_s64_if(pos + d0, (fw & has_next) ^ 1u);
+                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(pos + offk[k]);
+            }
             // segmented suffix XOR: v_l ^= v_{l+1} while linked
             uint32_t c = fw;
 #pragma unroll
             for (int d = 1; d < Q; d <<= 1) {
-                const uint64_t tv = __shfl_down_sync(0xffffffffu, v, 2 * d * G);
-                const uint32_t tc = __shfl_down_sync(0xffffffffu, c, 2 * d * G);
+                const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
+                const uint32_t tc = __shfl_down_sync(0xffffffffu, c, d * G);
                 if (c) {
                     v ^= tv;
                     c = tc;
                 }
             }
-            st_s64_if(pos, v, act);
+            st_s64_if(pos, v ^ own, act);
             pos += act ? stepb : 0;
             __syncwarp();
         }
@@ -537,10 +621,11 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                     for (int x = xk; x < P; x += XK) __stcs(o + x, buf[x * G]);
                 }
             } else {
+                // rows in bin order: pixel x at rowbase + P - 1 - x
                 uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
                 for (int ll = 0; ll < Q; ++ll) {
-                    const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
-                    for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, buf[x * G]);
+                    const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll] + (P - 1);
+                    for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, row[-x]);
                 }
             }
         }
@@ -1472,6 +1557,7 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
     a.reach = L.reach;
     a.RP = L.RP;
     a.SWc = L.SWc;
+    a.SWr = L.SWr;
     for (int l = 0; l < kMaxLines; ++l) a.rowbase[l] = L.rowbase[l];
     a.G = L.G;
     a.GS = L.GS;

@@ -1,6 +1,7 @@
 // Internal declarations of libmojette (host plan/schedule code and kernels).
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -44,6 +45,16 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 // Reconstruction path for one (geometry, erasure mask): Sec. 2.2's
 // pre-determined path with one projection dedicated to each line, run from
 // both ends of every line (a left-to-right and a right-to-left front).
+// Load order of a front that reads its words as numbered: own bin, then the
+// pixels on lines l + 1, l + 2, ... (mod Q).
+constexpr uint32_t kIdentityOrder = 0x76543210u;
+constexpr std::array<uint32_t, 2 * kMaxLines> identity_orders()
+{
+    std::array<uint32_t, 2 * kMaxLines> o{};
+    for (auto &v : o) v = kIdentityOrder;
+    return o;
+}
+
 struct Schedule {
     uint32_t mask = 0;
     int T = 0;                       // number of steps
@@ -77,6 +88,11 @@ struct Schedule {
     // the bank slots of its stripe groups), chosen so that the lanes of a
     // warp read different banks at the steps of this path (plan.cpp).
     int32_t rowoff[kMaxLines] = {};
+    int32_t rowpar[kMaxLines] = {};  // decode_lines: row phase parity for bulk staging
+    // decode_lines: load order of each front (index 2l + side), nibble k =
+    // the word its load instruction k reads (0: own bin, j >= 1: the pixel
+    // on line l + j mod Q); chosen with the row phases (plan.cpp).
+    std::array<uint32_t, 2 * kMaxLines> order = identity_orders();
     bool phases_done = false;
     // Two lines rebuilt (lines == 2): the closed form decode_scan2 solves,
     // with projection scan_proj[0] (direction scan_p[0]) dedicated to line 0
@@ -220,6 +236,7 @@ struct DecodeArgs {
     int64_t srcL[kMaxLines], srcR[kMaxLines];
     int32_t chunk_w, chunk_wait[kStreamChunks], chunk_done[kStreamChunks];
     int32_t rowoff[kMaxLines];
+    uint32_t order[2 * kMaxLines];  // decode_lines load orders (see Schedule)
     uint32_t *status;
 };
 int launch_decode(const DecodeArgs &a, cudaStream_t stream);
@@ -233,6 +250,7 @@ struct DecGroup {
     int32_t p[2 * kMaxLines];       // direction of front (l, side), index 2l + side
     int32_t src[2 * kMaxLines];     // bin of pixel x of that front: word src - x
     int32_t split[kMaxLines];       // x < split[l]: left front
+    uint32_t order[2 * kMaxLines];  // decode_lines: load order of each front (see Schedule)
     int32_t chunk_w;                // streamed chunks (see Schedule)
     int32_t chunk_wait[kStreamChunks];
     int32_t chunk_done[kStreamChunks];
@@ -259,6 +277,7 @@ struct DecWork {
 struct DecodeLayout {
     int kernel;         // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
     int reach, RP, SWc; // zero columns, row pitch, columns per stripe
+    int SWr = 0;        // decode_lines (not systematic): words per stripe region
     int G, GS;          // stripes per work item, their interleave stride
     int TS;             // words per step table (>= every group's steps, rounded)
     int rowbase[kMaxLines];   // first column of each line's row

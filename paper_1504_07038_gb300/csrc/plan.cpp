@@ -192,120 +192,200 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
             out->srcL[l] = sp > 0 ? pl.off[iL] + stored(iL, (int64_t)l * pl.p[iL] - pl.bmin[iL]) : 0;
             out->srcR[l] = sp < P ? pl.off[iR] + stored(iR, (int64_t)l * pl.p[iR] - sp - pl.bmin[iR]) + sp : 0;
         }
+        // Row parity for bulk staging (non-systematic decode_lines keeps a
+        // row in bin order, pixel x at row start + P - 1 - x): a front's run
+        // starts at bin src - x_last and lands at row start + P - 1 - x_last,
+        // so it is bulk-copied when the row start has the parity of
+        // src + 1 - P (stripe blocks of even length); the longer run decides.
+        const int nL = a[l], nR = P - a[l];
+        const int64_t parL = (out->srcL[l] + 1 - P) & 1, parR = (out->srcR[l] + 1 - P) & 1;
+        out->rowpar[l] = pl.systematic ? 0 : (int32_t)(nL >= nR ? parL : parR);
     }
     return out->T;
 }
 
-// Shared-memory bank phases of the lines for decode_lines (one lane per
-// (line, front, stripe); the G stripes of a lane group sit in G consecutive
-// 8-byte words, so a group fills one of S = 16 / G bank slots of a 128-byte
-// wavefront: slot = (row start + column) mod S). A warp's 64-bit load is
-// served per half-warp (lanes 0-15, 16-31; measured on GB300: the count of
-// load wavefronts follows this model, not a whole-warp one); within a half,
-// groups that read different words in the same slot serialise (a bank
-// conflict). The row phases e_l = (row start of line l) mod S are free: this
-// replays the path's loads -- the own bin and the other lines' pixels of
-// every front at every step, the forwarded operand excluded -- and picks the
-// phases that minimise the summed worst-slot occupancy of both halves (the
-// wavefronts), by coordinate descent from a few deterministic starts.
+// Shared-memory bank layout of decode_lines for one path: the row phases
+// (line l's row starts at a column congruent to rowoff[l] mod S) and the
+// order in which each front issues its loads.
+//
+// decode_lines runs one lane per (line, front, stripe): lane = side * 16 +
+// l * G + g, so the left fronts fill the lower half-warp and the right fronts
+// the upper one. The G stripes of a lane group sit in G consecutive 8-byte
+// words, one of S = 16 / G bank slots of a 128-byte wavefront: slot = (row
+// start + column) mod S. A warp's 64-bit load is served per half-warp
+// (measured on GB300: the count of load wavefronts follows this model, not a
+// whole-warp one), and within a half, groups that read different words in
+// the same slot serialise (a bank conflict). With each half holding fronts
+// that move the same way, the slots of a half keep their relative positions
+// in every step where all of its fronts move.
+//
+// Each front reads its own bin first, then XORs the other Q - 1 words of
+// the step (the pixels of the bin line on the other lines; a word line l+1
+// rebuilds in the same step is read too, and cancels on the device) in any
+// order: order[2l + side] holds in nibble k the word that load instruction
+// k reads (nibble 0 = 0, the own bin; j >= 1: the pixel on line l + j mod
+// Q). Choosing phases and orders so that each instruction meets distinct
+// slots is an edge colouring of the bipartite multigraph fronts x slots.
+//
+// This replays the path -- a front that does not move loads nothing -- and
+// costs a load instruction of a half the largest number of distinct words
+// one slot receives (its wavefronts); the store of the rebuilt pixels
+// counts the same way. Phases by coordinate descent and orders by pairwise
+// swaps, alternated, from a few deterministic starts.
 void choose_row_phases(const Plan &pl, Schedule *sc)
 {
     sc->phases_done = true;
     const int P = pl.P, Q = sc->lines;
-    for (int l = 0; l < kMaxLines; ++l) sc->rowoff[l] = 0;
+    for (int l = 0; l < kMaxLines; ++l) sc->rowoff[l] = sc->rowpar[l];
+    for (int f = 0; f < 2 * kMaxLines; ++f) sc->order[f] = kIdentityOrder;
+    (void)P;
     if (Q < 2 || Q > 8) return;
     const int G = std::max(1, 32 / (2 * Q));
     if (16 % G != 0 || G >= 16) return;
     const int S = 16 / G;
     const int T = sc->T;
+    // Non-systematic plans keep their rows in bin order (pixel x at row
+    // start + P - 1 - x), and a row's phase parity decides which of its
+    // fronts' runs are staged by bulk copies (rowpar, from the path); the
+    // search keeps that parity.
+    const bool rev = !pl.systematic;
+    const bool fixpar = rev && S % 2 == 0;
+    const int K = Q;          // words per front and step
+    const int F = 2 * Q;      // fronts, index side * Q + l
     // Every step is replayed to track the fronts; the cost counts at most
-    // 32 of them, evenly spaced.
-    const int stride = std::max(1, (T + 31) / 32);
+    // 96 of them, evenly spaced.
+    const int stride = std::max(1, (T + 95) / 96);
     const int TC = (T + stride - 1) / stride;
-    // loads[t / stride][k][front] = (line, column) or line -1: no access
-    struct Acc { int8_t line; int16_t col; };
-    const int K = Q;   // own + Q-1 operands
-    std::vector<Acc> acc((size_t)TC * K * 2 * Q);
+    // word j of front f at counted step c: (line << 16) | (column + 32768),
+    // or -1 (no load); the front's store likewise
+    auto key = [rev](int line, int col) {
+        if (rev) col = -col;
+        return (int32_t)((line << 16) | ((col + 32768) & 0xFFFF));
+    };
+    std::vector<int32_t> acc((size_t)TC * F * K, -1), sto((size_t)TC * F, -1);
     int x[2][kMaxLines];
     for (int l = 0; l < Q; ++l) { x[0][l] = 0; x[1][l] = P - 1; }
     for (int t = 0; t < T; ++t) {
-        const uint32_t w = sc->steps[(size_t)t], f = sc->fwdw[(size_t)t];
-        for (int l = 0; l < Q; ++l)
-            for (int side = 0; side < 2; ++side) {
-                const int fr = 2 * l + side;
-                const int p = side ? sc->pR[l] : sc->pL[l];
-                const int xx = x[side][l];
-                if (t % stride) continue;
-                Acc *a = &acc[((size_t)(t / stride) * K) * 2 * Q];
-                a[0 * 2 * Q + fr] = {(int8_t)l, (int16_t)xx};
-                for (int k = 0; k < Q - 1; ++k) {
-                    const int l2 = (l + 1 + k) % Q;
-                    const bool fwd = (k == 0 && l + 1 < Q && ((f >> fr) & 1u));
-                    a[(1 + k) * 2 * Q + fr] =
-                        fwd ? Acc{-1, 0} : Acc{(int8_t)l2, (int16_t)(xx + (sc->lpos[l2] - sc->lpos[l]) * p)};
+        const uint32_t w = sc->steps[(size_t)t];
+        if (t % stride == 0) {
+            const int c = t / stride;
+            for (int side = 0; side < 2; ++side)
+                for (int l = 0; l < Q; ++l) {
+                    const int bit = 2 * l + side;
+                    if (!((w >> bit) & 1u)) continue;
+                    const int f = side * Q + l;
+                    const int p = side ? sc->pR[l] : sc->pL[l];
+                    const int xx = x[side][l];
+                    sto[(size_t)c * F + f] = key(l, xx);
+                    int32_t *a = &acc[((size_t)c * F + f) * K];
+                    a[0] = key(l, xx);
+                    for (int j = 1; j < Q; ++j) {
+                        const int l2 = (l + j) % Q;
+                        a[j] = key(l2, xx + (sc->lpos[l2] - sc->lpos[l]) * p);
+                    }
                 }
-            }
+        }
         for (int l = 0; l < Q; ++l)
             for (int side = 0; side < 2; ++side)
                 if ((w >> (2 * l + side)) & 1u) x[side][l] += side ? -1 : 1;
     }
-    auto cost = [&](const int *e) {
+    int e[kMaxLines] = {};
+    uint8_t ord[2 * kMaxLines][kMaxLines];
+    // wavefronts of one set of words a half reads at once (k >= 0: load
+    // instruction k; k < 0: the store)
+    auto cost = [&](int h, int k) {
         int64_t c = 0;
-        int cnt[2][16];
-        Acc seen[2][16][16];
-        for (size_t b = 0; b < (size_t)TC * K; ++b) {
-            const Acc *a = &acc[b * 2 * Q];
-            for (int h = 0; h < 2; ++h)
-                for (int q = 0; q < S; ++q) cnt[h][q] = 0;
-            int worst[2] = {0, 0};
-            for (int fr = 0; fr < 2 * Q; ++fr) {
-                if (a[fr].line < 0) continue;
-                const int h = (fr * G) / 16;   // half-warp of the group's lanes
-                const int q = ((e[a[fr].line] + a[fr].col) % S + S) % S;
+        for (int t = 0; t < TC; ++t) {
+            int cnt[16] = {};
+            int32_t seen[16][kMaxLines];
+            int worst = 0;
+            for (int l = 0; l < Q; ++l) {
+                const int f = h * Q + l;
+                const int32_t kk = k < 0 ? sto[(size_t)t * F + f] : acc[((size_t)t * F + f) * K + ord[f][k]];
+                if (kk < 0) continue;
+                const int line = kk >> 16, col = (kk & 0xFFFF) - 32768;
+                const int q = ((e[line] + col) % S + S) % S;
                 bool dup = false;
-                for (int i = 0; i < cnt[h][q]; ++i)
-                    if (seen[h][q][i].line == a[fr].line && seen[h][q][i].col == a[fr].col) dup = true;
+                for (int i = 0; i < cnt[q]; ++i) dup = dup || seen[q][i] == kk;
                 if (dup) continue;
-                seen[h][q][cnt[h][q]++] = a[fr];
-                worst[h] = std::max(worst[h], cnt[h][q]);
+                seen[q][cnt[q]++] = kk;
+                worst = std::max(worst, cnt[q]);
             }
-            c += worst[0] + worst[1];
+            c += worst;
         }
         return c;
     };
-    int best[kMaxLines] = {}, e[kMaxLines];
+    int64_t part[2][kMaxLines + 1];
+    auto total = [&]() {
+        int64_t c = 0;
+        for (int h = 0; h < 2; ++h)
+            for (int k = -1; k < K; ++k) c += (part[h][k + 1] = cost(h, k));
+        return c;
+    };
+    int best_e[kMaxLines] = {};
+    uint8_t best_ord[2 * kMaxLines][kMaxLines];
     int64_t best_c = -1;
     uint32_t rng = 0x9E3779B9u ^ (uint32_t)(P * 131 + Q) ^ sc->mask;
-    for (int start = 0; start < 2; ++start) {
+    for (int start = 0; start < 3; ++start) {
         for (int l = 0; l < Q; ++l) {
             rng = rng * 1664525u + 1013904223u;
-            e[l] = start == 0 ? 0 : (int)(rng >> 16) % S;
+            e[l] = start == 0 ? 0 : (int)((rng >> 16) % (uint32_t)S);
+            if (fixpar && ((e[l] ^ sc->rowpar[l]) & 1)) e[l] = (e[l] + 1) % S;
         }
-        int64_t c = cost(e);
-        for (bool improved = true; improved;) {
-            improved = false;
+        for (int f = 0; f < F; ++f)
+            for (int k = 0; k < K; ++k) ord[f][k] = (uint8_t)k;
+        int64_t c = total();
+        for (int round = 0; round < 6; ++round) {
+            bool improved = false;
             for (int l = 0; l < Q; ++l) {
                 const int keep = e[l];
+                int bestv = keep;
                 for (int v = 0; v < S; ++v) {
-                    if (v == keep) continue;
+                    if (v == keep || (fixpar && ((v ^ sc->rowpar[l]) & 1))) continue;
                     e[l] = v;
-                    const int64_t cv = cost(e);
+                    const int64_t cv = total();
                     if (cv < c) {
                         c = cv;
+                        bestv = v;
                         improved = true;
-                    } else {
-                        e[l] = keep;
                     }
-                    if (e[l] != keep) break;
                 }
+                e[l] = bestv;
+                total();   // refresh the per-instruction parts
             }
+            for (int h = 0; h < 2; ++h)
+                for (int l = 0; l < Q; ++l) {
+                    const int f = h * Q + l;
+                    for (int a = 1; a < K; ++a)
+                        for (int b = a + 1; b < K; ++b) {
+                            std::swap(ord[f][a], ord[f][b]);
+                            const int64_t ca = cost(h, a), cb = cost(h, b);
+                            const int64_t d = ca + cb - part[h][a + 1] - part[h][b + 1];
+                            if (d < 0) {
+                                part[h][a + 1] = ca;
+                                part[h][b + 1] = cb;
+                                c += d;
+                                improved = true;
+                            } else {
+                                std::swap(ord[f][a], ord[f][b]);
+                            }
+                        }
+                }
+            if (!improved) break;
         }
         if (best_c < 0 || c < best_c) {
             best_c = c;
-            for (int l = 0; l < Q; ++l) best[l] = e[l];
+            for (int l = 0; l < Q; ++l) best_e[l] = e[l];
+            std::memcpy(best_ord, ord, sizeof(ord));
         }
     }
-    for (int l = 0; l < Q; ++l) sc->rowoff[l] = best[l];
+    for (int l = 0; l < Q; ++l) sc->rowoff[l] = best_e[l];
+    for (int side = 0; side < 2; ++side)
+        for (int l = 0; l < Q; ++l) {
+            uint32_t o = 0;
+            for (int k = 0; k < K; ++k) o |= (uint32_t)best_ord[side * Q + l][k] << (4 * k);
+            sc->order[2 * l + side] = o;
+        }
 }
 
 // Cap on the number of Q-subsets of the survivors tried per mask.

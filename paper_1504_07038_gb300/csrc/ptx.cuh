@@ -84,6 +84,13 @@ __device__ __forceinline__ void cp_async8(void *dst_smem, const void *src)
                  : "memory");
 }
 
+// 8-byte asynchronous copy global -> shared, the destination given as a
+// shared-memory address (both 8-byte aligned).
+__device__ __forceinline__ void cp_async8_s(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
 // Order this thread's earlier generic-proxy shared-memory writes before
 // later async-proxy (TMA) reads of them.
 __device__ __forceinline__ void fence_proxy_async_smem()
