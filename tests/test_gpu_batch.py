@@ -272,3 +272,50 @@ def test_batch_full_size_sampled():
         idx = np.unique(rng.integers(0, counts[k], 64))
         ref = oracle.decode(m.ref_proj[k][idx], p, P, Q, m.masks[k][idx], threads=8)
         assert np.array_equal(got[idx], ref)
+
+
+@pytest.mark.parametrize("P,Q,p", [(64, 8, TWELVE), (128, 8, TWELVE), (96, 6, [-4, -3, -2, -1, 1, 2, 3, 4])])
+def test_batch_decode_stripes_at_odd_word_offsets(P, Q, p):
+    """Decode stripes whose projection blocks and images start 8 bytes off a
+    16-byte boundary (the batch API asks for 8-byte alignment only): every
+    run of bins then disagrees mod 16 bytes with its place in shared memory
+    in half the stripes, so decode_lines stages those runs with the warp's
+    8-byte copies instead of bulk copies. Each stripe sits at its own odd or
+    even word offset; results equal the oracle's."""
+    S = 4500   # more than 4096: the launch also takes the path's row phases
+    n = len(p)
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(S, Q, P, seed=P * 7 + Q)
+    ref = oracle.encode(img, p, threads=8)
+    masks = inputs.erasure_masks(S, n, np.full(S, n - Q), seed=P + Q)
+    tot = plan.total
+    # stripe s at word s * (tot + 1) + 1 of its buffer: parities alternate
+    # with s when tot is even, and the first stripe is 8 bytes off
+    pw = tot + 1
+    pr = ref.copy()
+    offs, bins, _, _ = oracle.offsets(p, P, Q)
+    for i, (off, B) in enumerate(zip(offs, bins)):
+        pr[(masks >> i) & 1 == 1, off:off + B] = JUNK   # lost slices: junk
+    flat = np.full(S * pw + 2, JUNK, dtype=np.uint64)
+    for s in range(S):
+        flat[s * pw + 1:s * pw + 1 + tot] = pr[s]
+    d_src = torch.from_numpy(flat.view(np.int64)).cuda()
+    iw = Q * P + 1
+    d_out = torch.full((S * iw + 2,), 0x5A5A, dtype=torch.int64, device="cuda")
+    st = np.arange(S, dtype=np.uint64)
+    src = np.uint64(d_src.data_ptr()) + (st * np.uint64(pw) + np.uint64(1)) * np.uint64(8)
+    dst = np.uint64(d_out.data_ptr()) + (st * np.uint64(iw) + np.uint64(1)) * np.uint64(8)
+    table = mj.stripe_table([plan], np.zeros(S, dtype=np.int64), mj.MOJETTE_OP_DECODE, masks, src, dst)
+    batch = mj.mojette_batch_create(table, [plan])
+    assert mj.mojette_batch_info(batch)["launches"] >= 1
+    mj.mojette_batch_run(batch)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint64)
+    out = np.stack([got[s * iw + 1:s * iw + 1 + Q * P] for s in range(S)]).reshape(S, Q, P)
+    assert np.array_equal(out, img)
+    idx = np.arange(0, S, 97)
+    assert np.array_equal(out[idx], oracle.decode(ref[idx], p, P, Q, masks[idx], threads=8))
+    # the words between stripes are untouched
+    gaps = got[np.arange(S) * iw]
+    assert (gaps == np.uint64(0x5A5A)).all()
+    mj.mojette_batch_destroy(batch)
