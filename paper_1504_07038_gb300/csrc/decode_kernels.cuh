@@ -379,12 +379,14 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     const uint32_t bitmask = ok ? 1u << ls : 0u;
     const int myrow = a.rowbase[l];
     // Layouts. SYS: the G stripes interleaved word by word (word of column
-    // c of stripe g at (row + c) * G + g), rows in pixel order. Otherwise
-    // each stripe has its own region of SWr words (SWr = S mod 16, so the
-    // regions sit in different bank slots) with its rows in bin order --
-    // pixel x of line l at rowbase[l] + P - 1 - x -- the order of the
-    // dedicated projection's bins, so that a front's run of bins is staged
-    // by one bulk copy.
+    // c of stripe g at (row + c) * G + g), rows in pixel order, zero columns
+    // around them. Otherwise each stripe has its own region of SWr words
+    // (SWr = S mod 16, so the regions sit in different bank slots) with its
+    // rows in bin order -- pixel x of line l at rowbase[l] + P - 1 - x --
+    // the order of the dedicated projection's bins, so that a front's run
+    // of bins is staged by one bulk copy; one zero word sits before each
+    // row (column P in that order), and an operand column outside the image
+    // is clamped to it.
     const uint32_t start = SYS ? wbase + ((myrow + (side ? P - 1 : 0)) * G + g) * 8
                                : wbase + (g * a.SWr + myrow + (side ? 0 : P - 1)) * 8;
     const int stepb = SYS ? (side ? -1 : 1) * G * 8 : (side ? 8 : -8);
@@ -404,7 +406,9 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     // from the path's steady pattern: after the round with stride d, line l
     // is still linked iff it was, and line l+d was too.
     int T4 = 0;
-    int offk[Q > 1 ? Q - 1 : 1];
+    int offk[Q > 1 ? Q - 1 : 1];      // SYS: byte offset of operand k from this lane's word
+    int dk[Q > 1 ? Q - 1 : 1];        // otherwise: column offset (l2 - l) p of operand k
+    uint32_t rk[Q > 1 ? Q - 1 : 1];   //   and the address of column 0 of its line
     uint32_t sfw = 0u;
     uint32_t slink[4] = {0u, 0u, 0u, 0u};
     int chain = 0;   // steady steps: lines l+1 .. l+chain are linked to this one
@@ -423,7 +427,15 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         };
         const uint32_t ord = gr.order[ls];   // nibble 0 is the own bin
 #pragma unroll
-        for (int k = 1; k < Q; ++k) offk[k - 1] = off((l + ((ord >> (4 * k)) & 15u)) % Q);
+        for (int k = 1; k < Q; ++k) {
+            const int l2 = (l + ((ord >> (4 * k)) & 15u)) % Q;
+            if constexpr (SYS) {
+                offk[k - 1] = off(l2);
+            } else {
+                dk[k - 1] = (l2 - l) * p;
+                rk[k - 1] = wbase + (uint32_t)(g * a.SWr + a.rowbase[l2] + P - 1) * 8u;
+            }
+        }
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
         chain = 0;
         if (ok)
@@ -552,6 +564,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         }
 
         uint32_t pos = start;
+        int x = side ? P - 1 : 0;          // this front's column (not SYS)
+        const int dx = side ? -1 : 1;
+        // the word operand load k reads at this step
+        auto opaddr = [&](int k) -> uint32_t {
+            if constexpr (SYS) return pos + offk[k];
+            else return rk[k] - 8u * min((uint32_t)(x + dk[k]), (uint32_t)P);
+        };
         // the next step's words are read one step ahead (the tables hold
         // T4 + 4 words, so the read past the last step stays inside them)
         uint32_t w_next = stepw[0], f_next = fwdw[0];
@@ -564,7 +583,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 const uint64_t own = ld_s64(pos);
                 uint64_t v = 0;
 #pragma unroll
-                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(pos + offk[k]);
+                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(opaddr(k));
                 if constexpr (Q <= 4) {
                     // the linked lines' own values, all fetched at once: one
                     // shuffle latency instead of log2 Q dependent rounds
@@ -583,6 +602,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 }
                 st_s64_if(pos, v ^ own, ok);
                 pos += stepb;
+                x += dx;
                 __syncwarp();
                 continue;
             }
@@ -594,7 +614,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             if (act) {
                 own = ld_s64(pos);
 #pragma unroll
-                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(pos + offk[k]);
+                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(opaddr(k));
             }
             // segmented suffix XOR: v_l ^= v_{l+1} while linked
             uint32_t c = fw;
@@ -609,6 +629,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             }
             st_s64_if(pos, v ^ own, act);
             pos += act ? stepb : 0;
+            x += act ? dx : 0;
             __syncwarp();
         }
 

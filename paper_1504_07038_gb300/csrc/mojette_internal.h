@@ -286,7 +286,7 @@ struct DecodeLayout {
 // Q lines rebuilt whose image rows span `span` rows (Q - 1 unless
 // systematic); rowoff: decode_lines row offsets (may be null: none).
 int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig &cfg,
-                  const int32_t *rowoff, DecodeLayout *L);
+                  const int32_t *rowoff, DecodeLayout *L, bool sys = false);
 // Bank slots of one stripe group of decode_lines / decode_stream for Q lines.
 int decode_bank_slots(int Q);
 

@@ -227,10 +227,11 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
 // Q). Choosing phases and orders so that each instruction meets distinct
 // slots is an edge colouring of the bipartite multigraph fronts x slots.
 //
-// This replays the path -- a front that does not move loads nothing -- and
-// costs a load instruction of a half the largest number of distinct words
-// one slot receives (its wavefronts); the store of the rebuilt pixels
-// counts the same way. Phases by coordinate descent and orders by pairwise
+// This replays the path -- a front that does not move loads nothing, and
+// in the non-systematic layout every read of a line outside the image is
+// one word, the zero word before its row -- and costs a load instruction of
+// a half the largest number of distinct words one slot receives (its
+// wavefronts); the store of the rebuilt pixels counts the same way. Phases by coordinate descent and orders by pairwise
 // swaps, alternated, from a few deterministic starts.
 void choose_row_phases(const Plan &pl, Schedule *sc)
 {
@@ -281,7 +282,9 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
                     a[0] = key(l, xx);
                     for (int j = 1; j < Q; ++j) {
                         const int l2 = (l + j) % Q;
-                        a[j] = key(l2, xx + (sc->lpos[l2] - sc->lpos[l]) * p);
+                        int col = xx + (sc->lpos[l2] - sc->lpos[l]) * p;
+                        if (rev && (col < 0 || col >= P)) col = P;   // the zero word before the row
+                        a[j] = key(l2, col);
                     }
                 }
         }
