@@ -348,10 +348,9 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     constexpr int Q = QT;
     const int P = a.P, G = a.G;
     const int lane = threadIdx.x & 31;
-    // step words, forward words (TS words each), the staging mbarrier, then
-    // the slots
-    uint32_t *stepw = reinterpret_cast<uint32_t *>(sm);
-    uint32_t *fwdw = stepw + a.TS;
+    // (step word, forward word) pairs (TS of them), the staging mbarrier,
+    // then the slots
+    uint2 *stw = reinterpret_cast<uint2 *>(sm);
     uint64_t *mbar = sm + a.TS;
     uint64_t *wbuf = sm + a.TS + 2;
     // Zero the stripe slots once: rows are always staged before they are
@@ -415,10 +414,8 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     auto load_group = [&](const DecGroup &gr) {
         const int T = gr.T;
         T4 = (T + 3) & ~3;
-        for (int t = lane; t < T4; t += 32) {
-            stepw[t] = t < T ? gr.steps[t] : 0u;
-            fwdw[t] = t < T ? gr.steps[T + t] : 0u;
-        }
+        for (int t = lane; t < T4; t += 32)
+            stw[t] = t < T ? make_uint2(gr.steps[t], gr.steps[T + t]) : make_uint2(0u, 0u);
         // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
         const int p = gr.p[ls];
         auto off = [&](int l2) {
@@ -571,13 +568,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             if constexpr (SYS) return pos + offk[k];
             else return rk[k] - 8u * min((uint32_t)(x + dk[k]), (uint32_t)P);
         };
-        // the next step's words are read one step ahead (the tables hold
-        // T4 + 4 words, so the read past the last step stays inside them)
-        uint32_t w_next = stepw[0], f_next = fwdw[0];
+        // the next step's words are read one step ahead, as one 64-bit word
+        // (the table holds T4 + 4 pairs, so the read past the last step
+        // stays inside it)
+        uint2 nx = stw[0];
         for (int t = 0; t < T4; ++t) {
-            const uint32_t w = w_next, f = f_next;
-            w_next = stepw[t + 1];
-            f_next = fwdw[t + 1];
+            const uint32_t w = nx.x, f = nx.y;
+            nx = stw[t + 1];
             if (w & kStepSteady) {
                 // steady: every line moves, links are the path's pattern
                 const uint64_t own = ld_s64(pos);
