@@ -362,7 +362,9 @@ int build(Batch &b, const mojette_stripe_t *stripes, int64_t count, cudaStream_t
                 k.dcfg = def;
             if (big_sc)   // bulk-staging parity of the largest group's rows
                 for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = big_sc->rowpar[l];
-            if (big_sc && k.count >= kPhaseMinStripes) {
+            // the bank layout search serves the largest group's path: only
+            // worth its host time when that group alone is a large launch
+            if (big_sc && big >= kPhaseMinStripes) {
                 const int32_t *ph = schedule_row_phases(*k.plan, *big_sc);
                 for (int l = 0; l < kMaxLines; ++l) k.rowoff[l] = ph[l];
                 // its load orders go with those phases; the other groups

@@ -282,12 +282,13 @@ def test_batch_decode_stripes_at_odd_word_offsets(P, Q, p):
     in half the stripes, so decode_lines stages those runs with the warp's
     8-byte copies instead of bulk copies. Each stripe sits at its own odd or
     even word offset; results equal the oracle's."""
-    S = 4500   # more than 4096: the launch also takes the path's row phases
+    S = 4500
     n = len(p)
     plan = mj.mojette_plan(P, Q, p)
     img = inputs.stripes(S, Q, P, seed=P * 7 + Q)
     ref = oracle.encode(img, p, threads=8)
     masks = inputs.erasure_masks(S, n, np.full(S, n - Q), seed=P + Q)
+    masks[:4200] = masks[0]   # a group of 4200 stripes: its path's bank layout is searched
     tot = plan.total
     # stripe s at word s * (tot + 1) + 1 of its buffer: parities alternate
     # with s when tot is even, and the first stripe is 8 bytes off
