@@ -115,7 +115,7 @@ int class_layout(const Klass &k, const DecodeConfig &cfg, DecodeLayout *L)
     if (cfg.kernel == 4 && !k.scan_ok) return -EINVAL;
     if (cfg.kernel == 5 && !k.van_ok) return -EINVAL;
     return decode_layout(k.plan->P, k.lines, k.span, cfg.kernel == 5 ? k.van_maxp : k.maxp, k.maxT, cfg,
-                         k.rowoff, L, k.sys);
+                         k.rowoff, L);
 }
 
 // Lost data lines of a systematic decode stripe (0 otherwise).

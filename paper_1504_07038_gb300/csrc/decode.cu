@@ -36,7 +36,7 @@ int decode_bank_slots(int Q)
 }
 
 int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig &cfg,
-                  const int32_t *rowoff, DecodeLayout *L, bool sys)
+                  const int32_t *rowoff, DecodeLayout *L)
 {
     int err = 0, dev = 0, cap = 0, cap_sm = 0;
     if ((err = record_cuda(cudaGetDevice(&dev)))) return err;
@@ -104,40 +104,34 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
     }
     if (want == 0) {
         // decode_lines: 2Q lanes per stripe; step and forward words and the
-        // staging mbarrier (16 bytes) first. With row phases, line l's row
-        // starts at a column congruent to rowoff[l] mod S (the bank slots of
-        // a group of G words): the pitch gains S - 1 columns.
-        //   systematic: the G stripes interleaved word by word, `reach` zero
-        //     columns around every row (operands outside the image read them);
-        //   otherwise: each stripe in a region of SWr words, SWr = S mod 16
-        //     (stripe g's words g S bank slots further on; even: 16-byte
-        //     aligned regions), with one zero word before each row: an
-        //     operand column outside the image is clamped to P, which is
-        //     that word.
+        // staging mbarrier (16 bytes) first, then each stripe in a region
+        // of SWr words, SWr = S mod 16 (stripe g's words g S bank slots
+        // further on; even: 16-byte aligned regions). One zero word between
+        // rows (before row 0, after the last): an operand column outside
+        // the image is clamped to the word beside its row. With row phases,
+        // line l's row starts at a column congruent to rowoff[l] mod M, M =
+        // S (the bank slots of a group of G words), or 2 where no bank model
+        // applies (only the parity that lets bulk copies stage the row): the
+        // pitch gains M - 1 columns.
         L->G = std::max(1, 32 / (2 * Q));
         L->GS = L->G;
         const int S = decode_bank_slots(Q);
-        const int gap = sys ? L->reach : 1;
-        L->reach = gap;
-        L->RP = P + gap;
-        for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = gap + l * L->RP;
-        if (cfg.rowoff && rowoff && S > 1) {
-            L->RP = P + gap + (S - 1);
+        const int M = S > 1 ? S : 2;
+        L->reach = 1;
+        L->RP = P + 1;
+        for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = 1 + l * L->RP;
+        if (cfg.rowoff && rowoff) {
+            L->RP = P + 1 + (M - 1);
             for (int l = 0; l < Q; ++l) {
-                const int base = gap + l * L->RP;
-                L->rowbase[l] = base + (((rowoff[l] - base) % S) + S) % S;
+                const int base = 1 + l * L->RP;
+                L->rowbase[l] = base + (((rowoff[l] - base) % M) + M) % M;
             }
         }
-        L->SWc = Q * L->RP + gap;
-        if (sys) {
-            L->SWr = 0;
-            L->smem = (int64_t)L->TS * 8 + 16 + (int64_t)L->G * L->SWc * 8;
-        } else {
-            L->SWr = L->SWc;
-            const int want_mod = (S > 1) ? S : 2;
-            while (L->SWr % 16 != want_mod % 16 || L->SWr % 2) ++L->SWr;
-            L->smem = (int64_t)L->TS * 8 + 16 + (int64_t)L->G * L->SWr * 8;
-        }
+        L->SWc = Q * L->RP + 1;
+        L->SWr = L->SWc;
+        const int want_mod = (S > 1) ? S : 2;
+        while (L->SWr % 16 != want_mod % 16 || L->SWr % 2) ++L->SWr;
+        L->smem = (int64_t)L->TS * 8 + 16 + (int64_t)L->G * L->SWr * 8;
         return L->smem > cap ? -EINVAL : 0;   // one warp's stripes exceed shared memory
     }
     L->SWc = Q * L->RP + L->reach;
@@ -232,10 +226,10 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         // into the lost rows, then the path on them (decode_lines; no path
         // for one lost line)
         const int span = d.lpos[d.Q - 1] - d.lpos[0];
-        int err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L, true);
+        int err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
         if (err == -EINVAL && cfg.kernel == 4) {
             cfg.kernel = 0;
-            err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L, true);
+            err = decode_layout(d.P, d.Q, span, maxp, d.T, cfg, d.rowoff, &L);
         }
         if (err) return err;
         const int64_t nitems = (d.S + L.G - 1) / L.G;

@@ -9,8 +9,7 @@ int launch_decode_batched(const DecBatchArgs &b, const DecodeConfig &cfg, cudaSt
 {
     DecodeLayout L;
     if (b.sys && cfg.kernel != 0 && cfg.kernel != 4) return -EINVAL;
-    int err = decode_layout(b.P, b.Q, b.span, cfg.kernel == 5 ? b.van_maxp : b.maxp, b.maxT, cfg, b.rowoff, &L,
-                            b.sys);
+    int err = decode_layout(b.P, b.Q, b.span, cfg.kernel == 5 ? b.van_maxp : b.maxp, b.maxT, cfg, b.rowoff, &L);
     if (err) return err;
     DecParams a;
     std::memset(&a, 0, sizeof(a));

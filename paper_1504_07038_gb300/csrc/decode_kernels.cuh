@@ -64,7 +64,7 @@ struct DecParams {
     int reach;    // zero columns before, between and after the rows of a stripe
     int RP;       // row pitch in columns: P + reach (+ room for row phases)
     int SWc;      // columns per stripe slot
-    int SWr;      // decode_lines (not systematic): words per stripe region
+    int SWr;      // decode_lines: words per stripe region
     int rowbase[kMaxLines];   // decode_lines: first column of each line's row
     int G;        // stripes per work item (one warp)
     int GS;       // interleave stride (decode_lines: G; decode_fronts: G rounded to odd)
@@ -346,21 +346,22 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
 {
     extern __shared__ __align__(16) uint64_t sm[];
     constexpr int Q = QT;
+    // Rows of the non-systematic form are kept in bin order (see below).
+    constexpr bool REV = !SYS;
     const int P = a.P, G = a.G;
     const int lane = threadIdx.x & 31;
     // (step word, forward word) pairs (TS of them), the staging mbarrier,
-    // then the slots
+    // then the stripes' regions
     uint2 *stw = reinterpret_cast<uint2 *>(sm);
     uint64_t *mbar = sm + a.TS;
     uint64_t *wbuf = sm + a.TS + 2;
-    // Zero the stripe slots once: rows are always staged before they are
-    // read and the columns around them (pixels outside the image, the XOR
-    // identity) are never written.
-    const int slot_words = SYS ? a.SWc * G : a.SWr * G;
-    for (int i = lane; i < slot_words; i += 32) wbuf[i] = 0;
+    // Zero the regions once: rows are always staged before they are read,
+    // and the word beside each row (a pixel outside the image, the XOR
+    // identity) is never written.
+    for (int i = lane; i < a.SWr * G; i += 32) wbuf[i] = 0;
     const uint32_t wbase = smem_addr(wbuf);
     const uint32_t bar = smem_addr(mbar);
-    if (!SYS && lane == 0) {
+    if (lane == 0) {
         mbar_init(bar, 32);   // every lane arrives once per item
         mbar_init_fence();
     }
@@ -377,37 +378,37 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     const int ls = 2 * l + side;   // front index in the step words
     const uint32_t bitmask = ok ? 1u << ls : 0u;
     const int myrow = a.rowbase[l];
-    // Layouts. SYS: the G stripes interleaved word by word (word of column
-    // c of stripe g at (row + c) * G + g), rows in pixel order, zero columns
-    // around them. Otherwise each stripe has its own region of SWr words
-    // (SWr = S mod 16, so the regions sit in different bank slots) with its
-    // rows in bin order -- pixel x of line l at rowbase[l] + P - 1 - x --
-    // the order of the dedicated projection's bins, so that a front's run
-    // of bins is staged by one bulk copy; one zero word sits before each
-    // row (column P in that order), and an operand column outside the image
-    // is clamped to it.
-    const uint32_t start = SYS ? wbase + ((myrow + (side ? P - 1 : 0)) * G + g) * 8
-                               : wbase + (g * a.SWr + myrow + (side ? 0 : P - 1)) * 8;
-    const int stepb = SYS ? (side ? -1 : 1) * G * 8 : (side ? 8 : -8);
+    // Layout: each stripe has its own region of SWr words (SWr = S mod 16,
+    // so the regions sit in different bank slots), row l starting at
+    // rowbase[l]. The non-systematic form keeps a row in bin order -- pixel
+    // x at rowbase[l] + P - 1 - x, the order of the dedicated projection's
+    // bins, so that a front's run of bins is staged by one bulk copy -- and
+    // the systematic form in pixel order (x at rowbase[l] + x), the order of
+    // the residual rows it is staged from. One zero word sits beside each
+    // row, at column P in the row's order; an operand column outside the
+    // image is clamped to it (one unsigned min).
+    const uint32_t start = wbase + (g * a.SWr + myrow + ((side == 0) == REV ? P - 1 : 0)) * 8;
+    const int stepb = (side == 0) == REV ? -8 : 8;
 
     // Path-dependent state. A front reads Q words per step: its own bin
     // (first) and the pixels of the bin line on lines l + j (mod Q), j = 1 ..
-    // Q-1; j = 1 is line l+1, which may be rebuilt by its front in this same
-    // step (forwarded), except for l = Q-1 where it wraps to line 0.
-    // offk[k]: byte offset of the word operand load k reads, k = 0 .. Q-2 (the
-    // path's load order, chosen with the row phases so that each load
-    // instruction meets distinct bank slots). A forwarded word is read all
-    // the same: it still holds line l+1's bin, which line l+1 reads as its
-    // own, so the chain runs over b = pixel ^ own bin -- b_l = (XOR of l's
-    // operand words) ^ b_{l+1} while linked, pixel_l = b_l ^ own bin_l --
-    // and the stale bin cancels. For steady steps: this lane's link (line l
-    // forwards from line l+1) and the link state after each scan round,
-    // from the path's steady pattern: after the round with stride d, line l
-    // is still linked iff it was, and line l+d was too.
+    // Q-1, at column x + (row of l2 - row of l) p; j = 1 is line l+1, which
+    // may be rebuilt by its front in this same step (forwarded), except for
+    // l = Q-1 where it wraps to line 0. Operand k (the path's load order,
+    // chosen with the row phases so that each load instruction meets
+    // distinct bank slots) sits dk[k] columns from this front's pixel, on
+    // the line whose column 0 is at byte address rk[k]. A forwarded word is
+    // read all the same: it still holds line l+1's bin, which line l+1
+    // reads as its own, so the chain runs over b = pixel ^ own bin -- b_l =
+    // (XOR of l's operand words) ^ b_{l+1} while linked, pixel_l = b_l ^ own
+    // bin_l -- and the stale bin cancels. For steady steps: this lane's link
+    // (line l forwards from line l+1), the number of lines linked after it,
+    // and the link state after each scan round, from the path's steady
+    // pattern: after the round with stride d, line l is still linked iff it
+    // was, and line l+d was too.
     int T4 = 0;
-    int offk[Q > 1 ? Q - 1 : 1];      // SYS: byte offset of operand k from this lane's word
-    int dk[Q > 1 ? Q - 1 : 1];        // otherwise: column offset (l2 - l) p of operand k
-    uint32_t rk[Q > 1 ? Q - 1 : 1];   //   and the address of column 0 of its line
+    int dk[Q > 1 ? Q - 1 : 1];
+    uint32_t rk[Q > 1 ? Q - 1 : 1];
     uint32_t sfw = 0u;
     uint32_t slink[4] = {0u, 0u, 0u, 0u};
     int chain = 0;   // steady steps: lines l+1 .. l+chain are linked to this one
@@ -416,22 +417,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         T4 = (T + 3) & ~3;
         for (int t = lane; t < T4; t += 32)
             stw[t] = t < T ? make_uint2(gr.steps[t], gr.steps[T + t]) : make_uint2(0u, 0u);
-        // bytes from this lane's pixel to pixel (l2, x + (l2 - l) p)
         const int p = gr.p[ls];
-        auto off = [&](int l2) {
-            if constexpr (SYS) return (a.rowbase[l2] - myrow + (gr.lpos[l2] - gr.lpos[l]) * p) * G * 8;
-            else return (a.rowbase[l2] - myrow - (l2 - l) * p) * 8;
-        };
         const uint32_t ord = gr.order[ls];   // nibble 0 is the own bin
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             const int l2 = (l + ((ord >> (4 * k)) & 15u)) % Q;
-            if constexpr (SYS) {
-                offk[k - 1] = off(l2);
-            } else {
-                dk[k - 1] = (l2 - l) * p;
-                rk[k - 1] = wbase + (uint32_t)(g * a.SWr + a.rowbase[l2] + P - 1) * 8u;
-            }
+            dk[k - 1] = (gr.lpos[l2] - gr.lpos[l]) * p;
+            rk[k - 1] = wbase + (uint32_t)(g * a.SWr + a.rowbase[l2] + (REV ? P - 1 : 0)) * 8u;
         }
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
         chain = 0;
@@ -458,8 +450,8 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     if constexpr (!BATCHED) load_group(a.grp);
     __syncwarp();
 
-    // Copy lanes: lane = xk * G + gg covers XK columns of G stripes (the G
-    // stripes of a column on adjacent lanes: contiguous shared-memory words).
+    // Copy lanes (write-back): lane = xk * G + gg covers XK columns of G
+    // stripes.
     const int XK = 32 / G;
     const int xk = lane / G, gg = lane - xk * G;
     const bool copy_ok = xk < XK;
@@ -488,33 +480,29 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             nst = (int)min64(G, a.S - s0);
         }
 
-        if constexpr (SYS) {
-            // the residual bins, in pixel order, in the lost rows
-            if (copy_ok && gg < nst) {
-                const uint64_t *dat = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
-                for (int ll = 0; ll < Q; ++ll) {
-                    const uint64_t *srow = dat + (int64_t)grp().lpos[ll] * P;
-                    uint64_t *dst = wbuf + a.rowbase[ll] * G + gg;
-                    for (int x = xk; x < P; x += XK) cp_async8(dst + x * G, srow + x);
+        // Staging: each lane copies one run of n consecutive words in row
+        // order -- non-systematic: its own front's run of bins of its
+        // dedicated projection (bins src - x for the pixels x the front
+        // rebuilds); systematic: the lanes of the left side each a whole
+        // residual row. Where the run and its place in shared memory agree
+        // mod 16 bytes, one bulk copy takes the aligned middle and 8-byte
+        // cp.async the odd word at either end; the other runs are copied by
+        // the whole warp, word by word. The previous item's reads and
+        // writes of the regions are ordered before the bulk writes first.
+        fence_proxy_async_smem();
+        __syncwarp();
+        int n = 0;
+        const uint64_t *gsrc = nullptr;
+        uint32_t sdst = 0;
+        if (ok && g < nst) {
+            if constexpr (SYS) {
+                if (side == 0) {
+                    const uint64_t *dat = BATCHED ? a.dstp[first + g] : a.img + (s0 + g) * (int64_t)a.Qd * P;
+                    n = P;
+                    gsrc = dat + (int64_t)grp().lpos[l] * P;
+                    sdst = wbase + (g * a.SWr + myrow) * 8;
                 }
-            }
-            cp_async_wait_all();
-            __syncwarp();
-        } else {
-            // Each lane stages its own front's run of bins: n consecutive
-            // words of its dedicated projection (bins src - x for the pixels
-            // x the front rebuilds), in bin order, which is the row order.
-            // Where the run and its place in shared memory agree mod 16
-            // bytes, one bulk copy takes the aligned middle and 8-byte
-            // cp.async the odd word at either end; the other runs are copied
-            // by the whole warp, word by word. The previous item's reads and
-            // writes of the slots are ordered before the bulk writes first.
-            fence_proxy_async_smem();
-            __syncwarp();
-            int n = 0;
-            const uint64_t *gsrc = nullptr;
-            uint32_t sdst = 0;
-            if (ok && g < nst) {
+            } else {
                 const uint64_t *sb = BATCHED ? a.srcp[first + g] : a.proj + (s0 + g) * a.total;
                 const int sp = grp().split[l];
                 if (side == 0) {
@@ -527,46 +515,46 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                     sdst = wbase + (g * a.SWr + myrow) * 8;
                 }
             }
-            const bool same = n > 0 && ((((uint32_t)(uintptr_t)gsrc) ^ sdst) & 8u) == 0;
-            const int head = same && ((uintptr_t)gsrc & 8u) ? 1 : 0;
-            const int body = same ? ((n - head) & ~1) : 0;
-            mbar_arrive_expect_tx(bar, (uint32_t)body * 8u);
-            if (body > 0) tma_load_1d(sdst + head * 8u, gsrc + head, (uint32_t)body * 8u, bar);
-            if (same) {
-                if (head) cp_async8_s(sdst, gsrc);
-                if (n - head - body) cp_async8_s(sdst + (uint32_t)(n - 1) * 8u, gsrc + (n - 1));
-            }
-            uint32_t rest = __ballot_sync(0xffffffffu, n > 0 && !same);
-            while (rest) {
-                const int src_lane = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const int nn = __shfl_sync(0xffffffffu, n, src_lane);
-                const uint64_t *gs = reinterpret_cast<const uint64_t *>(
-                    __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)gsrc, src_lane));
-                const uint32_t sd = __shfl_sync(0xffffffffu, sdst, src_lane);
-                for (int i = lane; i < nn; i += 32) cp_async8_s(sd + (uint32_t)i * 8u, gs + i);
-            }
-            cp_async_wait_all();
-            const bool arrived = mbar_wait_bounded(bar, phase);
-            phase ^= 1u;
-            if (__any_sync(0xffffffffu, !arrived)) {
-                // the bulk copies did not land in time: report, let any
-                // still in flight finish (bounded) and stop
-                if (lane == 0) atomicOr(a.status, kStatusWaitTimeout);
-                mbar_wait_bounded(bar, phase ^ 1u);
-                dead = true;
-                return;
-            }
-            __syncwarp();
         }
+        const bool same = n > 0 && ((((uint32_t)(uintptr_t)gsrc) ^ sdst) & 8u) == 0;
+        const int head = same && ((uintptr_t)gsrc & 8u) ? 1 : 0;
+        const int body = same ? ((n - head) & ~1) : 0;
+        mbar_arrive_expect_tx(bar, (uint32_t)body * 8u);
+        if (body > 0) tma_load_1d(sdst + head * 8u, gsrc + head, (uint32_t)body * 8u, bar);
+        if (same) {
+            if (head) cp_async8_s(sdst, gsrc);
+            if (n - head - body) cp_async8_s(sdst + (uint32_t)(n - 1) * 8u, gsrc + (n - 1));
+        }
+        uint32_t rest = __ballot_sync(0xffffffffu, n > 0 && !same);
+        while (rest) {
+            const int src_lane = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int nn = __shfl_sync(0xffffffffu, n, src_lane);
+            const uint64_t *gs = reinterpret_cast<const uint64_t *>(
+                __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)gsrc, src_lane));
+            const uint32_t sd = __shfl_sync(0xffffffffu, sdst, src_lane);
+            for (int i = lane; i < nn; i += 32) cp_async8_s(sd + (uint32_t)i * 8u, gs + i);
+        }
+        cp_async_wait_all();
+        const bool arrived = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+        if (__any_sync(0xffffffffu, !arrived)) {
+            // the bulk copies did not land in time: report, let any still in
+            // flight finish (bounded) and stop
+            if (lane == 0) atomicOr(a.status, kStatusWaitTimeout);
+            mbar_wait_bounded(bar, phase ^ 1u);
+            dead = true;
+            return;
+        }
+        __syncwarp();
 
         uint32_t pos = start;
-        int x = side ? P - 1 : 0;          // this front's column (not SYS)
+        int x = side ? P - 1 : 0;          // this front's column
         const int dx = side ? -1 : 1;
         // the word operand load k reads at this step
         auto opaddr = [&](int k) -> uint32_t {
-            if constexpr (SYS) return pos + offk[k];
-            else return rk[k] - 8u * min((uint32_t)(x + dk[k]), (uint32_t)P);
+            const uint32_t c = 8u * min((uint32_t)(x + dk[k]), (uint32_t)P);
+            return REV ? rk[k] - c : rk[k] + c;
         };
         // the next step's words are read one step ahead, as one 64-bit word
         // (the table holds T4 + 4 pairs, so the read past the last step
@@ -584,10 +572,10 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 if constexpr (Q <= 4) {
                     // the linked lines' own values, all fetched at once: one
                     // shuffle latency instead of log2 Q dependent rounds
-                    const uint64_t x = v;
+                    const uint64_t x0 = v;
 #pragma unroll
                     for (int d = 1; d < Q; ++d) {
-                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x, d * G);
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x0, d * G);
                         if (d <= chain) v ^= tv;
                     }
                 } else {
@@ -630,20 +618,21 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             __syncwarp();
         }
 
+        // write-back, coalesced along each row: the image's lines (the lost
+        // data lines, in place, for the systematic form)
         if (copy_ok && gg < nst) {
             if constexpr (SYS) {
                 uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
                 for (int ll = 0; ll < Q; ++ll) {
-                    const uint64_t *buf = wbuf + a.rowbase[ll] * G + gg;
+                    const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll];
                     uint64_t *o = out + (int64_t)grp().lpos[ll] * P;
-                    for (int x = xk; x < P; x += XK) __stcs(o + x, buf[x * G]);
+                    for (int xx = xk; xx < P; xx += XK) __stcs(o + xx, row[xx]);
                 }
             } else {
-                // rows in bin order: pixel x at rowbase + P - 1 - x
                 uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
                 for (int ll = 0; ll < Q; ++ll) {
                     const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll] + (P - 1);
-                    for (int x = xk; x < P; x += XK) __stcs(out + ll * P + x, row[-x]);
+                    for (int xx = xk; xx < P; xx += XK) __stcs(out + ll * P + xx, row[-xx]);
                 }
             }
         }

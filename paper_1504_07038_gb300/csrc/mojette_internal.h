@@ -277,7 +277,7 @@ struct DecWork {
 struct DecodeLayout {
     int kernel;         // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
     int reach, RP, SWc; // zero columns, row pitch, columns per stripe
-    int SWr = 0;        // decode_lines (not systematic): words per stripe region
+    int SWr = 0;        // decode_lines: words per stripe region
     int G, GS;          // stripes per work item, their interleave stride
     int TS;             // words per step table (>= every group's steps, rounded)
     int rowbase[kMaxLines];   // first column of each line's row
@@ -286,7 +286,7 @@ struct DecodeLayout {
 // Q lines rebuilt whose image rows span `span` rows (Q - 1 unless
 // systematic); rowoff: decode_lines row offsets (may be null: none).
 int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig &cfg,
-                  const int32_t *rowoff, DecodeLayout *L, bool sys = false);
+                  const int32_t *rowoff, DecodeLayout *L);
 // Bank slots of one stripe group of decode_lines / decode_stream for Q lines.
 int decode_bank_slots(int Q);
 

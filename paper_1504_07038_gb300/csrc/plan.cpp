@@ -228,8 +228,8 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
 // slots is an edge colouring of the bipartite multigraph fronts x slots.
 //
 // This replays the path -- a front that does not move loads nothing, and
-// in the non-systematic layout every read of a line outside the image is
-// one word, the zero word before its row -- and costs a load instruction of
+// every read of a line outside the image is one word, the zero word beside
+// its row -- and costs a load instruction of
 // a half the largest number of distinct words one slot receives (its
 // wavefronts); the store of the rebuilt pixels counts the same way. Phases by coordinate descent and orders by pairwise
 // swaps, alternated, from a few deterministic starts.
@@ -246,11 +246,12 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
     const int S = 16 / G;
     const int T = sc->T;
     // Non-systematic plans keep their rows in bin order (pixel x at row
-    // start + P - 1 - x), and a row's phase parity decides which of its
-    // fronts' runs are staged by bulk copies (rowpar, from the path); the
-    // search keeps that parity.
+    // start + P - 1 - x), systematic ones in pixel order. A row's phase
+    // parity decides which of its runs are staged by bulk copies (rowpar:
+    // from the path, or even for the residual rows of a systematic decode);
+    // the search keeps that parity.
     const bool rev = !pl.systematic;
-    const bool fixpar = rev && S % 2 == 0;
+    const bool fixpar = S % 2 == 0;
     const int K = Q;          // words per front and step
     const int F = 2 * Q;      // fronts, index side * Q + l
     // Every step is replayed to track the fronts; the cost counts at most
@@ -283,7 +284,7 @@ void choose_row_phases(const Plan &pl, Schedule *sc)
                     for (int j = 1; j < Q; ++j) {
                         const int l2 = (l + j) % Q;
                         int col = xx + (sc->lpos[l2] - sc->lpos[l]) * p;
-                        if (rev && (col < 0 || col >= P)) col = P;   // the zero word before the row
+                        if (col < 0 || col >= P) col = P;   // the zero word beside the row
                         a[j] = key(l2, col);
                     }
                 }
