@@ -197,6 +197,8 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
         // starts at bin src - x_last and lands at row start + P - 1 - x_last,
         // so it is bulk-copied when the row start has the parity of
         // src + 1 - P (stripe blocks of even length); the longer run decides.
+        // A systematic decode stages whole residual rows, which start at
+        // even words of the data buffer when P is even: even row starts.
         const int nL = a[l], nR = P - a[l];
         const int64_t parL = (out->srcL[l] + 1 - P) & 1, parR = (out->srcR[l] + 1 - P) & 1;
         out->rowpar[l] = pl.systematic ? 0 : (int32_t)(nL >= nR ? parL : parR);
@@ -210,14 +212,15 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
 //
 // decode_lines runs one lane per (line, front, stripe): lane = side * 16 +
 // l * G + g, so the left fronts fill the lower half-warp and the right fronts
-// the upper one. The G stripes of a lane group sit in G consecutive 8-byte
-// words, one of S = 16 / G bank slots of a 128-byte wavefront: slot = (row
-// start + column) mod S. A warp's 64-bit load is served per half-warp
-// (measured on GB300: the count of load wavefronts follows this model, not a
-// whole-warp one), and within a half, groups that read different words in
-// the same slot serialise (a bank conflict). With each half holding fronts
-// that move the same way, the slots of a half keep their relative positions
-// in every step where all of its fronts move.
+// the upper one. The G stripes of a warp sit in regions that start S = 16 / G
+// bank slots (8-byte words mod 16) apart, so the G lanes of a front that read
+// the same position of their stripes fill one slot class of a 128-byte
+// wavefront: class = (row start + position) mod S. A warp's 64-bit load is
+// served per half-warp (measured on GB300: the count of load wavefronts
+// follows this model, not a whole-warp one), and within a half, fronts that
+// read different words of the same class serialise (a bank conflict). With
+// each half holding fronts that move the same way, the classes of a half keep
+// their relative positions in every step where all of its fronts move.
 //
 // Each front reads its own bin first, then XORs the other Q - 1 words of
 // the step (the pixels of the bin line on the other lines; a word line l+1
@@ -229,17 +232,16 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
 //
 // This replays the path -- a front that does not move loads nothing, and
 // every read of a line outside the image is one word, the zero word beside
-// its row -- and costs a load instruction of
-// a half the largest number of distinct words one slot receives (its
-// wavefronts); the store of the rebuilt pixels counts the same way. Phases by coordinate descent and orders by pairwise
-// swaps, alternated, from a few deterministic starts.
+// its row -- and costs a load instruction of a half the largest number of
+// distinct words one class receives (its wavefronts); the store of the
+// rebuilt pixels counts the same way. Phases by coordinate descent and
+// orders by pairwise swaps, alternated, from three deterministic starts.
 void choose_row_phases(const Plan &pl, Schedule *sc)
 {
     sc->phases_done = true;
     const int P = pl.P, Q = sc->lines;
     for (int l = 0; l < kMaxLines; ++l) sc->rowoff[l] = sc->rowpar[l];
     for (int f = 0; f < 2 * kMaxLines; ++f) sc->order[f] = kIdentityOrder;
-    (void)P;
     if (Q < 2 || Q > 8) return;
     const int G = std::max(1, 32 / (2 * Q));
     if (16 % G != 0 || G >= 16) return;
