@@ -284,6 +284,30 @@ int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask,
                      uint32_t *steps, uint32_t *forward, int64_t max_steps,
                      int64_t *n_steps);
 
+/*
+ * mojette_schedule_layout -- the shared-memory layout decode_lines uses for
+ * the cached reconstruction path of one erasure mask in launches of 4096 or
+ * more stripes, copied out for inspection (host only, touches no device; the
+ * first call for a mask runs the search, tens of milliseconds at Q = 8, and
+ * the result is kept with the path). The paper has no counterpart: this is
+ * a GPU bank layout, not part of the inverse transform (Sec. 2.2), whose
+ * result it does not change.
+ *   row_phase[lines]   receives, per rebuilt line, the residue mod S of its
+ *                      row's first shared-memory word (S = 16 / G bank-slot
+ *                      classes, G = 32 / (2 Q) stripes per warp; where no
+ *                      bank model applies, Q = 3, 5 or Q > 8, only a parity);
+ *                      its parity lets bulk copies stage the row's bins;
+ *   load_order[2*lines] receives, per front (index 2l + side, side 0: left
+ *                      to right), its load order: nibble k = the word load
+ *                      instruction k reads, 0 the front's own bin, j >= 1
+ *                      the pixel on line l + j mod Q (nibble 0 is 0).
+ * `lines` is Q (a systematic plan: the lost data lines, as mojette_schedule
+ * counts them). Either pointer may be NULL. Errors: -EINVAL,
+ * -ENOTRECOVERABLE, -ENOMEM.
+ */
+int mojette_schedule_layout(mojette_plan_t plan, uint32_t erasure_mask, int32_t *row_phase,
+                            uint32_t *load_order);
+
 /* ------------------------------------------------------------------------
  * Batches: many stripes of mixed geometry, operation (encode or decode) and
  * erasure pattern in one submission. The paper codes one block at a time

@@ -58,6 +58,7 @@ def lib():
             L.mojette_sys_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_kernel.argtypes = [_PTR, _U32, _I64, ctypes.POINTER(ctypes.c_int32)]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
+            L.mojette_schedule_layout.argtypes = [_PTR, _U32, _PTR, _PTR]
             L.mojette_batch_create.argtypes = [_PTR, _I64, _U32, ctypes.POINTER(_PTR)]
             L.mojette_batch_update.argtypes = [_PTR, _PTR, _I64, _PTR]
             L.mojette_batch_run.argtypes = [_PTR, _PTR]
@@ -80,7 +81,8 @@ def lib():
                          "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc", "mojette_sys_decode",
                          "mojette_decode_kernel",
-                         "mojette_schedule", "mojette_batch_create", "mojette_batch_update",
+                         "mojette_schedule", "mojette_schedule_layout", "mojette_batch_create",
+                         "mojette_batch_update",
                          "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
                          "mojette_batch_destroy", "mojette_server_create", "mojette_server_submit",
                          "mojette_server_poll", "mojette_server_now", "mojette_server_stats",
@@ -323,6 +325,20 @@ def mojette_schedule(plan: Plan, erasure_mask: int) -> dict:
         lines = bin(int(erasure_mask) & ((1 << Q) - 1)).count("1")
     return {"left": list(left)[:lines], "right": list(right)[:lines], "split": list(split)[:lines],
             "steps": list(steps)[:T], "forward": list(forward)[:T], "T": T, "lines": lines}
+
+
+def mojette_schedule_layout(plan: Plan, erasure_mask: int) -> dict:
+    """decode_lines' shared-memory layout for one mask's path (host data):
+    per-line row phases and per-front load orders (nibbles)."""
+    lines = plan.Q
+    if plan.systematic:
+        lines = bin(int(erasure_mask) & ((1 << plan.Q) - 1)).count("1")
+    n = max(lines, 1)
+    phase = (ctypes.c_int32 * n)()
+    order = (ctypes.c_uint32 * (2 * n))()
+    _check(lib().mojette_schedule_layout(plan.handle, int(erasure_mask) & 0xFFFFFFFF, phase, order),
+           "mojette_schedule_layout")
+    return {"row_phase": list(phase)[:lines], "load_order": list(order)[:2 * lines], "lines": lines}
 
 
 # ---- batches -----------------------------------------------------------------

@@ -386,6 +386,29 @@ int mojette_schedule(mojette_plan_t plan, uint32_t erasure_mask, int32_t *surviv
     return 0;
 }
 
+int mojette_schedule_layout(mojette_plan_t plan, uint32_t erasure_mask, int32_t *row_phase,
+                            uint32_t *load_order)
+{
+    if (!plan) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->Q > kMaxLines) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    // the search runs once per path and is kept with it; once done, the
+    // phases and orders never change
+    const int32_t *ph = schedule_row_phases(*pl, *sc);
+    for (int l = 0; l < sc->lines; ++l) {
+        if (row_phase) row_phase[l] = ph[l];
+        if (load_order) {
+            load_order[2 * l] = sc->order[2 * l];
+            load_order[2 * l + 1] = sc->order[2 * l + 1];
+        }
+    }
+    return 0;
+}
+
 int mojette_device_status(uint32_t *flags, int clear)
 {
     int err = 0;

@@ -396,3 +396,127 @@ def test_decode_kernel_choice():
         assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_lines"
     finally:
         del os.environ["MOJETTE_DECODE_KERNEL"]
+
+
+# ---- decode_lines' shared-memory layout (mojette_schedule_layout) ------------
+
+def _bank_model_cost(P, Q, p, sched, phase, orders, rev):
+    """Wavefronts of decode_lines' loads and stores under the half-warp bank
+    model, replaying the path: a half-warp holds the fronts of one side; a
+    load instruction of a half costs the largest number of distinct words
+    one slot class (row phase + position, mod S) receives; a front that does
+    not move loads nothing; a read outside the image is the zero word beside
+    its row (column P)."""
+    G = 32 // (2 * Q)
+    S = 16 // G
+    x = [[0] * Q, [P - 1] * Q]
+    cost = 0
+    for t in range(sched["T"]):
+        w = sched["steps"][t]
+        for side in (0, 1):
+            per_k = [dict() for _ in range(Q)]
+            store = {}
+            for l in range(Q):
+                if not (w >> (2 * l + side)) & 1:
+                    continue
+                pp = p[sched["right"][l] if side else sched["left"][l]]
+                xx = x[side][l]
+                words = [(l, xx)]
+                for j in range(1, Q):
+                    l2 = (l + j) % Q
+                    c = xx + (l2 - l) * pp
+                    words.append((l2, c if 0 <= c < P else P))
+
+                def cls(word):
+                    return (phase[word[0]] + (-word[1] if rev else word[1])) % S
+                o = orders[2 * l + side]
+                for k in range(Q):
+                    word = words[(o >> (4 * k)) & 15]
+                    per_k[k].setdefault(cls(word), set()).add(word)
+                store.setdefault(cls(words[0]), set()).add(words[0])
+            cost += sum(max(len(v) for v in d.values()) for d in per_k if d)
+            cost += max((len(v) for v in store.values()), default=0)
+        for l in range(Q):
+            for side in (0, 1):
+                if (w >> (2 * l + side)) & 1:
+                    x[side][l] += -1 if side else 1
+    return cost
+
+
+def _run_parity(P, Q, p, plan, sched, l):
+    """Parity of a row start that lets a bulk copy stage the longer of line
+    l's two runs of bins (rows in bin order: pixel x at start + P - 1 - x;
+    the left run of bins src - x, x < split, lands at start + P - split)."""
+    _, offs, _ = mj.mojette_plan_info(plan)
+
+    def src(i):
+        bmin = -(P - 1) + min(0, (Q - 1) * p[i])
+        return offs[i] + l * p[i] - bmin
+    sp = sched["split"][l]
+    parL = (src(sched["left"][l]) + 1 - P) & 1
+    parR = (src(sched["right"][l]) + 1 - P) & 1
+    return parL if sp >= P - sp else parR
+
+
+@pytest.mark.parametrize("P,Q,p", CONFIGS)
+def test_schedule_layout_invariants_and_bank_cost(P, Q, p):
+    """The bank layout of every sampled mask: each front reads its own bin
+    first and every other word of the step exactly once; row phases are
+    slot classes with the parity that stages the longer run of each line by
+    bulk copy; the search is deterministic, costs no more wavefronts (bank
+    model; the search itself scores at most 96 evenly spaced steps) than
+    plain orders with the same parities, and at Q = 8 at least 20% fewer."""
+    plan = mj.mojette_plan(P, Q, p)
+    n = len(p)
+    G = 32 // (2 * Q)
+    S = 16 // G
+    masks = inputs.all_masks(n, n - Q)
+    masks = masks[:: max(1, len(masks) // 12)]
+    for m in masks:
+        lay = mj.mojette_schedule_layout(plan, m)
+        assert lay == mj.mojette_schedule_layout(plan, m)
+        sched = mj.mojette_schedule(plan, m)
+        for f, o in enumerate(lay["load_order"]):
+            nib = [(o >> (4 * k)) & 15 for k in range(Q)]
+            assert nib[0] == 0, (m, f)
+            assert sorted(nib[1:]) == list(range(1, Q)), (m, f, nib)
+        for l, e in enumerate(lay["row_phase"]):
+            assert 0 <= e < S
+            assert e % 2 == _run_parity(P, Q, p, plan, sched, l), (m, l)
+        plain = [sum(k << (4 * k) for k in range(Q))] * (2 * Q)
+        parity = [_run_parity(P, Q, p, plan, sched, l) for l in range(Q)]
+        got = _bank_model_cost(P, Q, p, sched, lay["row_phase"], lay["load_order"], True)
+        ref = _bank_model_cost(P, Q, p, sched, parity, plain, True)
+        assert got <= 1.01 * ref, (m, got, ref)
+        if Q == 8:
+            assert got <= 0.8 * ref, (m, got, ref)
+
+
+def test_schedule_layout_systematic_rows_even_and_no_bank_model_parity_only():
+    """Systematic paths keep even row phases (their residual rows start at
+    even words); a geometry with no bank model (Q = 3: five stripes per
+    warp) gets only the staging parity and plain load orders."""
+    sysplan = mj.mojette_plan_ex(128, 8, [-2, -1, 1, 2], mj.MOJETTE_PLAN_SYSTEMATIC)
+    for lost in ([0, 3, 5], [1, 2, 6, 7], [2, 4]):
+        m = sum(1 << i for i in lost)
+        lay = mj.mojette_schedule_layout(sysplan, m)
+        assert lay["lines"] == len(lost)
+        assert all(e % 2 == 0 for e in lay["row_phase"]), lay
+    p = [-2, -1, 1, 2, 3]
+    plan = mj.mojette_plan(96, 3, p)
+    for m in inputs.all_masks(len(p), 2):
+        lay = mj.mojette_schedule_layout(plan, m)
+        sched = mj.mojette_schedule(plan, m)
+        assert lay["row_phase"] == [_run_parity(96, 3, p, plan, sched, l) for l in range(3)]
+        assert all(o & 0xFFF == 0x210 for o in lay["load_order"]), lay
+
+
+def test_schedule_layout_validates_arguments():
+    plan = mj.mojette_plan(128, 4, [-3, -2, -1, 1, 2, 3])
+    with pytest.raises(mj.MojetteError) as ei:
+        mj.mojette_schedule_layout(plan, 1 << 9)          # bit beyond n
+    assert ei.value.code == -errno.EINVAL
+    with pytest.raises(mj.MojetteError) as ei:
+        mj.mojette_schedule_layout(plan, 0b000111)        # three lost: two survivors short
+    assert ei.value.code == -errno.ENOTRECOVERABLE
+    assert mj.lib().mojette_schedule_layout(None, 0, None, None) == -errno.EINVAL
