@@ -14,18 +14,21 @@
 // dependency along the lines (about P/2 steps per stripe with two fronts),
 // so the kernels are built to keep that chain short and many stripes in
 // flight:
-//   - the pixel line l+1 rebuilt in the same step is forwarded in a
-//     register, so the only shared-memory round trip on the critical path
-//     is one per step;
-//   - the 64-bit words of the G stripes of a warp are interleaved in shared
-//     memory (word = column * stride + stripe), so lanes that run the same
-//     front of different stripes read one contiguous run: no bank conflicts;
-//   - the Q*P bins the path uses are staged in pixel order by 8-byte
-//     cp.async copies (coalesced; the descending bin order costs nothing)
-//     and each rebuilt pixel overwrites its own bin, so a stripe needs Q*P
-//     words of shared memory plus zero columns around the rows;
-//   - the zero columns stand for pixels outside the image (the XOR
-//     identity), so no bounds test sits in the inner loop.
+//   - the pixel line l+1 rebuilt in the same step is forwarded through
+//     registers (warp shuffles), so the only shared-memory round trip on the
+//     critical path is one per step;
+//   - the Q*P bins the path uses are staged in shared memory and each
+//     rebuilt pixel overwrites its own bin, so a stripe needs about Q*P words
+//     of shared memory;
+//   - a pixel outside the image reads a zero word (the XOR identity), so no
+//     bounds test sits in the inner loop.
+// decode_lines, the default path kernel, keeps each stripe in its own region
+// with rows in the order of the bins it stages (one bulk copy per front's run
+// of bins), one zero word beside each row (operand columns outside the image
+// are clamped to it), and a per-path bank layout chosen on the host (row
+// phases and per-front load orders). decode_fronts, decode_cols and
+// decode_stream interleave the G stripes of a warp word by word, staged by
+// 8-byte cp.async into rows with zero columns around them.
 //
 // Every kernel comes in two forms: plain (one reconstruction path, stripes
 // back to back at fixed strides) and batched (work items of G stripes, each
@@ -329,12 +332,13 @@ __global__ void __launch_bounds__(32) decode_fronts(const __grid_constant__ DecP
 // decode_lines: one lane per (stripe, line, front). A warp holds G = 32/(2Q)
 // stripes; at every step each lane rebuilds the next pixel of its line's
 // front (when the step word moves it), from its staged bin and the other
-// pixels of the bin line read from shared memory -- except the operand on
+// pixels of the bin line read from shared memory -- except the value on
 // line l+1, which line l+1 may rebuild in this same step. Those same-step
 // links (bit 2l+side of the step's forward word) form chains l -> l+1 -> ...
 // within a front; the chain values are a segmented suffix XOR over the lines,
 // done with log2(Q) rounds of warp shuffles, so every lane of every line
-// works at every step and a step costs one shared-memory round trip.
+// works at every step and a step costs one shared-memory round trip. The
+// layout, the staging and the addressing are described in the kernel.
 //
 // SYS: the systematic form. The lines rebuilt are the lost data lines (Q of
 // them, at image rows lpos[]) of the data buffer (img, or dstp[s] batched, Qd
