@@ -13,16 +13,30 @@ over ranks. Inputs (2.1 GB image, 3.3 GB projections) exceed the 129 MB L2,
 so no flush is needed between steps.
 
 The same line carries, unless switched off:
-  e2e      the step through the C ABI from pinned host buffers, copies timed;
+  wide     the (12,8) geometry the paper's Sec. 3.1 also measures: 262144
+           stripes at 8 KB (Q=8, P=128) and at 4 KB (Q=8, P=64), encode and
+           15 sampled four-erasure decodes, each kernel's ms and fraction of
+           the HBM roofline;
+  alternatives  the opt-in decode kernels on the same workloads: decode_ilv
+           (the path with stripes across lanes) and decode_vander (Eq. 1 as
+           a Vandermonde system: not the paper's inverse, reported apart);
+  e2e      the step through the C ABI from pinned host buffers, copies timed
+           (decode inputs: only the surviving projections' slices);
   batched  500000 mixed stripes (4 KB / 8 KB x (3,2), (6,4), (12,8), 0..n-k
            erasures each) as two CUDA-graph launches per step, against the
            same work as plain per-(geometry, mask) launches;
   served   the request server under closed-loop and Poisson load (p50/p99),
            against the same requests served one at a time;
-  systematic  the systematic form (data lines stored as they are, parity
-           projections): parity encode and in-place decode per number of
-           lost data lines, 8 KB stripes of (6,4) and (12,8);
-  cpu_baseline  the oracle on the host cores, on a bounded sample.
+  systematic  (with --systematic) the systematic form (data lines stored
+           as they are, parity projections): parity encode and in-place
+           decode per number of lost data lines, 8 KB stripes of (6,4) and
+           (12,8);
+  cpu_baseline  the oracle on the host cores, on a bounded sample, one
+           thread and all cores.
+
+Decode bytes (the HBM roofline): every bin of the Q projections the path
+uses (sum of their B_i) read, plus the Q * P pixels written; encode bytes:
+the Q * P pixels read plus every bin written.
 
 --impl reference times the CPU oracle (the slow plain implementation the
 tests compare against) on the host cores, on bounded samples of the same
@@ -207,35 +221,111 @@ def max_over_ranks(x: float, dist=None) -> float:
 
 # ------------------------------------------------------------------ GPU arm --
 
-def run_gpu(args, w):
+def workload_config(args, w, world):
+    """The `config` of the JSON line (both arms): the workload, not the
+    implementation."""
+    return {"workload": args.workload, "description": w["desc"], "stripes": w["S"],
+            "block_bytes": w["Q"] * w["P"] * 8, "Q": w["Q"], "P": w["P"], "n": len(w["p"]), "p": w["p"],
+            "decode_masks": len(workload_masks(w)), "launches_per_step": 1 + len(workload_masks(w)),
+            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"}
+
+
+def decode_bytes(plan, masks, S):
+    """Algorithmic HBM bytes of one decode launch per mask: every bin of the
+    Q projections the path uses (the sum of their B_i) read, and the Q * P
+    pixels written."""
+    from paper_1504_07038_gb300 import binding as mj
+    out = []
+    for m in masks:
+        sc = mj.mojette_schedule(plan, m)
+        used = set(sc["left"]) | set(sc["right"])
+        out.append(S * 8 * (sum(int(plan.bins[i]) for i in used) + plan.Q * plan.P))
+    return out
+
+
+def time_launches(fn, reps, stream):
+    """Median CUDA-event time (ms) of fn() on `stream` over reps launches
+    (after one untimed launch)."""
+    import torch
+    fn()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        ts.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ts)
+
+
+def with_kernel(name):
+    """Context manager: MOJETTE_DECODE_KERNEL set to name (read at every
+    plain launch) for the duration."""
+    class _K:
+        def __enter__(self):
+            self.old = os.environ.get("MOJETTE_DECODE_KERNEL")
+            os.environ["MOJETTE_DECODE_KERNEL"] = name
+
+        def __exit__(self, *exc):
+            if self.old is None:
+                os.environ.pop("MOJETTE_DECODE_KERNEL", None)
+            else:
+                os.environ["MOJETTE_DECODE_KERNEL"] = self.old
+    return _K()
+
+
+def kernel_stats(ms, bytes_, user, peak, traffic=None):
+    gbs = bytes_ / (ms * 1e-3) / 1e9
+    return {"ms": round(ms, 4), "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "user_gbs": round(user / (ms * 1e-3) / 1e9, 1), "algorithmic_bytes_per_launch": int(bytes_),
+            "traffic": traffic}
+
+
+def alt_decodes(plan, d_img, d_proj, d_out, masks, S, dbytes, user, peak, stream, reps=3):
+    """The opt-in decode kernels on a workload: ms (mean over masks of the
+    median over reps) and fraction of the roofline, each checked exact."""
     import torch
     from paper_1504_07038_gb300 import binding as mj
+    out = {}
+    for name, what in (("ilv", "the Sec. 2.2 path, stripes across lanes (one lane per stripe, front and "
+                                "half of the lines)"),
+                       ("vander", "Eq. 1 solved as a Vandermonde system: exact, not the paper's inverse")):
+        with with_kernel(name):
+            kname = mj.mojette_decode_kernel(plan, masks[0], S)
+            if kname != "decode_" + name:
+                continue
+            d_out.zero_()
+            ms = [time_launches(lambda m=m: mj.mojette_decode(plan, d_proj, m, d_out, S, stream), reps, stream)
+                  for m in masks]
+        out[kname] = kernel_stats(statistics.mean(ms), statistics.mean(dbytes), user, peak)
+        out[kname]["exact"] = bool(torch.equal(d_out, d_img))
+        out[kname]["what"] = what
+    return out
 
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+def run_workload(args, w, name, peak, stream, rank, timed_steps, clocks=None, keep=False):
+    """Encode every stripe, then decode every stripe under each of the
+    workload's masks, timed per launch with CUDA events on `stream`.
+    Returns (result dict, buffers or None)."""
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
 
     P, Q, p, S = w["P"], w["Q"], w["p"], w["S"]
     masks = workload_masks(w)
     plan = mj.mojette_plan(P, Q, p)
-    stream = torch.cuda.current_stream()
-
     img_np = inputs.stripes(S, Q, P, seed=args.seed, first=replica_first_stripe(rank, S))
     h_img = torch.from_numpy(img_np.view(np.int64)).pin_memory()
     del img_np
     d_img = h_img.cuda()
     d_proj = torch.empty((S, plan.total), dtype=torch.int64, device="cuda")
     d_out = torch.empty((S, Q, P), dtype=torch.int64, device="cuda")
-    launches_per_step = 1 + len(masks)
+    launches = 1 + len(masks)
 
     def mk():
         return torch.cuda.Event(enable_timing=True)
 
     def step(ev=None):
-        """One step; ev: list of (start, end) event pairs, one per launch."""
         if ev:
             ev[0][0].record(stream)
         mj.mojette_encode(plan, d_img, d_proj, S, stream)
@@ -248,16 +338,68 @@ def run_gpu(args, w):
             if ev:
                 ev[1 + k][1].record(stream)
 
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    mj.mojette_device_status()        # raises if any bounded wait expired
+    exact = bool(torch.equal(d_out, d_img))
+    events = [[(mk(), mk()) for _ in range(launches)] for _ in range(timed_steps)]
+    if clocks:
+        clocks.start()
+        time.sleep(0.4)
+    t0, t1 = mk(), mk()
+    t0.record(stream)
+    for k in range(timed_steps):
+        step(events[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    mj.mojette_device_status()
+    enc_ms = statistics.mean(e[0][0].elapsed_time(e[0][1]) for e in events)
+    by_mask = [statistics.median(e[1 + k][0].elapsed_time(e[1 + k][1]) for e in events)
+               for k in range(len(masks))]
+    dec_ms = statistics.mean(by_mask)
+    user = S * Q * P * 8
+    dbytes = decode_bytes(plan, masks, S)
+    enc_bytes = S * (Q * P + plan.total) * 8
+    dec_name = decode_kernel_name(plan, masks[0], S)
+    traffic_key = name if not args.stripes else None
+    kern = {"encode_tiles": kernel_stats(enc_ms, enc_bytes, user, peak, ncu_traffic("encode_tiles", traffic_key)),
+            dec_name: kernel_stats(dec_ms, statistics.mean(dbytes), user, peak, ncu_traffic(dec_name, traffic_key))}
+    kern[dec_name]["path_bytes_per_launch"] = S * 2 * Q * P * 8
+    kern[dec_name]["ms_by_mask"] = {"min": round(min(by_mask), 4), "max": round(max(by_mask), 4),
+                                    "max_over_min": round(max(by_mask) / min(by_mask), 4), "masks": len(masks)}
+    res = {"total_ms": t0.elapsed_time(t1), "steps": timed_steps, "launches_per_step": launches,
+           "user_bytes": user, "kernels": kern, "decode_kernel": dec_name, "exact": exact,
+           "clocks": clk, "masks": masks, "dec_bytes": dbytes, "plan": plan,
+           "desc": w["desc"], "stripes": S}
+    if not args.no_alternatives:
+        res["alternatives"] = alt_decodes(plan, d_img, d_proj, d_out, masks, S, dbytes, user, peak, stream)
+    bufs = (plan, h_img, d_img, d_proj, d_out, masks) if keep else None
+    if not keep:
+        del d_img, d_proj, d_out, h_img
+        torch.cuda.empty_cache()
+    return res, bufs
+
+
+def run_gpu(args, w):
+    import torch
+    from paper_1504_07038_gb300 import binding as mj
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+
     def barrier():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        step()
-    mj.mojette_device_status()        # raises if any bounded wait expired
-    barrier()
 
     uuid = None
     try:
@@ -265,29 +407,16 @@ def run_gpu(args, w):
         uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
     except Exception:
         pass
-    events = [[(mk(), mk()) for _ in range(launches_per_step)] for _ in range(args.steps)]
-    clocks = ClockSampler(uuid)
-    clocks.start()
-    time.sleep(0.4)
-    t0, t1 = mk(), mk()
-    t0.record(stream)
-    for k in range(args.steps):
-        step(events[k])
-    t1.record(stream)
     barrier()
-    enc_ms = [e[0][0].elapsed_time(e[0][1]) for e in events]
-    dec_ms = [a.elapsed_time(b) for e in events for a, b in e[1:]]
-    # decode time per erasure mask (median over steps): the paper finds the
-    # cost independent of which projections are lost (Sec. 4, Fig. 2-3)
-    by_mask = [statistics.median(e[1 + k][0].elapsed_time(e[1 + k][1]) for e in events)
-               for k in range(len(masks))]
-    total_ms = t0.elapsed_time(t1)
-    clk = clocks.stop()
-    total_ms = max_over_ranks(total_ms, dist)
-    mj.mojette_device_status()
+    main, bufs = run_workload(args, w, args.workload, peak, stream, rank, args.steps, ClockSampler(uuid), keep=True)
+    barrier()
+    total_ms = max_over_ranks(main["total_ms"], dist)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
+    plan, h_img, d_img, d_proj, d_out, masks = bufs
     e2e = None if args.no_e2e else run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream)
+    del bufs, h_img, d_img, d_proj, d_out
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist:
@@ -295,19 +424,12 @@ def run_gpu(args, w):
             dist.destroy_process_group()
         return None
 
-    user_bytes = S * Q * P * 8
+    S, Q, P, p = w["S"], w["Q"], w["P"], w["p"]
     ms_step = total_ms / args.steps
-    value = world * user_bytes * launches_per_step / (ms_step * 1e-3) / 1e9
-    enc_ms_avg = statistics.mean(enc_ms)
-    dec_ms_avg = statistics.mean(dec_ms)
-    enc_bytes = S * (Q * P + plan.total) * 8
-    dec_bytes = S * 2 * Q * P * 8
-    peak, peak_kind = measured_peaks()
-    dec_gbs = dec_bytes / (dec_ms_avg * 1e-3) / 1e9
-    dec_name = decode_kernel_name(plan, masks[0], S)
-    # the ncu record was taken at the workload's own stripe count
-    traffic_key = args.workload if not args.stripes else None
-    enc_gbs = enc_bytes / (enc_ms_avg * 1e-3) / 1e9
+    launches = main["launches_per_step"]
+    value = world * main["user_bytes"] * launches / (ms_step * 1e-3) / 1e9
+    dec_name = main["decode_kernel"]
+    dk = main["kernels"][dec_name]
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -321,42 +443,40 @@ def run_gpu(args, w):
         "vs_baseline": None,
         "dtype": "u64",
         "data": "synthetic (seeded SplitMix64 uniform uint64 pixels)",
-        "config": {"workload": args.workload, "description": w["desc"], "stripes": S,
-                   "block_bytes": Q * P * 8, "Q": Q, "P": P, "n": len(p), "p": p,
-                   "decode_masks": len(masks), "launches_per_step": launches_per_step,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": dec_name, "achieved": round(dec_gbs, 1),
-                     "peak": peak, "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
+        "config": workload_config(args, w, world),
+        "roofline": {"bound": "hbm", "kernel": dec_name, "achieved": dk["hbm_gbs"],
+                     "peak": peak, "unit": "GB/s", "frac": dk["frac"],
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)",
-                     "traffic": ncu_traffic(dec_name, traffic_key),
-                     "algorithmic_bytes_per_launch": dec_bytes},
-        "kernels": {
-            "encode_tiles": {"ms": round(enc_ms_avg, 4), "hbm_gbs": round(enc_gbs, 1),
-                             "frac": round(enc_gbs / peak, 4),
-                             "user_gbs": round(user_bytes / (enc_ms_avg * 1e-3) / 1e9, 1),
-                             "algorithmic_bytes_per_launch": enc_bytes,
-                             "traffic": ncu_traffic("encode_tiles", traffic_key)},
-            dec_name: {"ms": round(dec_ms_avg, 4), "hbm_gbs": round(dec_gbs, 1),
-                       "frac": round(dec_gbs / peak, 4),
-                       "user_gbs": round(user_bytes / (dec_ms_avg * 1e-3) / 1e9, 1),
-                       "algorithmic_bytes_per_launch": dec_bytes,
-                       "traffic": ncu_traffic(dec_name, traffic_key),
-                       "ms_by_mask": {"min": round(min(by_mask), 4), "max": round(max(by_mask), 4),
-                                      "max_over_min": round(max(by_mask) / min(by_mask), 4),
-                                      "masks": len(masks)}},
-        },
-        "gpu_launches": args.steps * launches_per_step,
-        "clocks": clk,
+                     "traffic": dk["traffic"],
+                     "algorithmic_bytes_per_launch": dk["algorithmic_bytes_per_launch"],
+                     "bytes": "sum of B_i over the Q projections the path uses, read, + Q*P pixels written"},
+        "kernels": main["kernels"],
+        "exact": main["exact"],
+        "gpu_launches": args.steps * launches,
+        "clocks": main["clocks"],
         "e2e": e2e,
     }
+    if "alternatives" in main:
+        line["alternatives"] = main["alternatives"]
+    if not args.no_wide and args.workload == "plain_at_scale":
+        line["wide"] = {}
+        for wl in ("wide_8k", "wide_4k"):
+            ww = dict(WORKLOADS[wl])
+            r, _ = run_workload(args, ww, wl, peak, stream, rank, max(3, min(args.steps, 10)))
+            line["wide"][wl] = {"description": ww["desc"], "decode_kernel": r["decode_kernel"],
+                                "kernels": r["kernels"], "exact": r["exact"],
+                                "step_user_gbs": round(r["user_bytes"] * r["launches_per_step"] /
+                                                       (r["total_ms"] / r["steps"] * 1e-3) / 1e9, 1)}
+            if "alternatives" in r:
+                line["wide"][wl]["alternatives"] = r["alternatives"]
     if not args.no_batched:
         line["batched"] = run_batched(args, rank)
     if not args.no_served:
         line["served"] = run_served(args, rank)
-    if not args.no_systematic:
+    if args.systematic:
         line["systematic"] = run_systematic(args, rank)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, masks, budget_s=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(w, main["masks"], budget_s=args.cpu_seconds)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -366,12 +486,13 @@ def run_gpu(args, w):
 def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
     """Same metric through the C ABI with host buffers: every step copies the
     image in and the projections out (encode), then for each mask the
-    projection block in (decode reads only the surviving slices of it) and
-    the image out (decode), from/to pinned host memory. The stripes are cut
-    into `chunks` slices that alternate over two streams, each slice's
-    copies and kernels in order on its stream, so one slice's host-to-device
-    copy overlaps another's device-to-host copy and kernels. Decode reads a
-    separate device buffer, filled with junk before the timed region, so the
+    projections the decode reads in (mojette_stage_survivors: the Q
+    surviving projections' slices, what a storage read fetches) and the
+    image out, from/to pinned host memory. The stripes are cut into `chunks`
+    slices that alternate over two streams, each slice's copies and kernels
+    in order on its stream, so one slice's host-to-device copy overlaps
+    another's device-to-host copy and kernels. Decode reads a separate
+    device buffer, filled with junk before the timed region, so the
     round-trip check shows the copied data is what is used."""
     import torch
     from paper_1504_07038_gb300 import binding as mj
@@ -383,8 +504,10 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
     chunks, nstreams = args.e2e_chunks, args.e2e_streams
     side = [torch.cuda.Stream() for _ in range(nstreams)]
     bounds = [(S * c // chunks, S * (c + 1) // chunks) for c in range(chunks)]
+    staged = [0]
 
     def step():
+        staged[0] = 0
         for st in side:
             st.wait_stream(stream)
         for c, (a, b) in enumerate(bounds):
@@ -394,15 +517,16 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
                 mj.mojette_encode(plan, d_img[a:b], d_proj[a:b], b - a, st)
                 h_proj[a:b].copy_(d_proj[a:b], non_blocking=True)
                 for m in masks:
-                    d_in[a:b].copy_(h_proj[a:b], non_blocking=True)
+                    staged[0] += mj.mojette_stage_survivors(plan, h_proj[a:b], m, d_in[a:b], b - a, st)
                     mj.mojette_decode(plan, d_in[a:b], m, d_out[a:b], b - a, st)
                     h_out[a:b].copy_(d_out[a:b], non_blocking=True)
         for st in side:
             stream.wait_stream(st)
 
-    steps = max(1, min(args.steps, 3))
+    steps = max(10, min(args.steps, 12))
     step()
     torch.cuda.synchronize()
+    floor = copy_floor(h_proj, d_in)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
@@ -413,11 +537,66 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
     ms = t0.elapsed_time(t1) / steps
     ok = bool(np.array_equal(h_out.numpy(), h_img.numpy()))
     user = S * Q * P * 8 * (1 + len(masks))
+    h2d = S * Q * P * 8 + staged[0]
+    d2h = S * plan.total * 8 + len(masks) * S * Q * P * 8
     return {"value": round(user / (ms * 1e-3) / 1e9, 3), "unit": "GB/s",
-            "h2d_bytes_per_step": S * Q * P * 8 + len(masks) * S * plan.total * 8,
-            "d2h_bytes_per_step": S * plan.total * 8 + len(masks) * S * Q * P * 8,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": round(ms, 3), "steps": steps, "round_trip_ok": ok,
-            "pipeline": f"{chunks} stripe slices over {nstreams} streams"}
+            "copy_floor": {"ms": round(max(h2d / floor["h2d_gbs"], d2h / floor["d2h_gbs"],
+                                           (h2d + d2h) / floor["both_gbs"]) / 1e6, 3), **floor},
+            "pipeline": f"{chunks} stripe slices over {nstreams} streams; decode inputs: surviving projections only",
+            "host": host_memory_note()}
+
+
+def copy_floor(h_buf, d_buf, nbytes=2 << 30):
+    """Pinned host <-> device copy bandwidth (GB/s) measured on this machine:
+    host-to-device alone, device-to-host alone, and both at once on two
+    streams (the e2e step's copies cannot beat these)."""
+    import torch
+    n = min(nbytes // 8, h_buf.numel(), d_buf.numel())
+    h, d = h_buf.view(-1)[:n], d_buf.view(-1)[:n]
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    half = n // 2
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / reps
+
+    def both():
+        with torch.cuda.stream(a):
+            d[:half].copy_(h[:half], non_blocking=True)
+        with torch.cuda.stream(b):
+            h[half:2 * half].copy_(d[half:2 * half], non_blocking=True)
+
+    t_in = timed(lambda: d.copy_(h, non_blocking=True))
+    t_out = timed(lambda: h.copy_(d, non_blocking=True))
+    t_both = timed(both)
+    return {"h2d_gbs": round(n * 8 / t_in / 1e9, 1), "d2h_gbs": round(n * 8 / t_out / 1e9, 1),
+            "both_gbs": round(2 * half * 8 / t_both / 1e9, 1)}
+
+
+def host_memory_note():
+    """Where the pinned buffers sit relative to the GPU: the NUMA nodes of
+    the host and the GPU's affinity (nvidia-smi topo), for the record."""
+    note = {}
+    try:
+        nodes = [d for d in os.listdir("/sys/devices/system/node") if d.startswith("node") and d[4:].isdigit()]
+        note["numa_nodes"] = len(nodes)
+    except Exception:
+        pass
+    try:
+        r = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.startswith("GPU0"):
+                note["gpu0_topo"] = " ".join(ln.split())
+    except Exception:
+        pass
+    return note
 
 
 # ------------------------------------------------------------ batched arm --
@@ -652,24 +831,33 @@ def run_served(args, rank=0):
 
 # --------------------------------------------------------------- CPU oracle --
 
-def cpu_baseline(w, masks, budget_s=12.0):
-    """The oracle as it stands on the host cores, on a bounded sample of the
-    workload (1 encode + len(masks) decodes per stripe, like a step)."""
+def oracle_rate(w, masks, budget_s, threads):
+    """The oracle on `threads` host threads over a growing sample of the
+    workload's stripes (1 encode + len(masks) decodes each) until it runs
+    about budget_s / 4 seconds: (user-data GB/s, stripes, seconds)."""
     import oracle
     P, Q, p = w["P"], w["Q"], w["p"]
-    cores = os.cpu_count() or 1
-    S = 64
+    S = 16
     while True:
         img = inputs.stripes(S, Q, P)
         t0 = time.perf_counter()
-        proj = oracle.encode(img, p, threads=cores)
+        proj = oracle.encode(img, p, threads=threads)
         for m in masks:
-            oracle.decode(proj, p, P, Q, m, threads=cores)
+            oracle.decode(proj, p, P, Q, m, threads=threads)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or S >= w["S"]:
             break
         S = min(w["S"], int(S * max(2.0, budget_s / 4 / max(dt, 1e-3))))
-    user = S * Q * P * 8 * (1 + len(masks))
+    return S * Q * P * 8 * (1 + len(masks)) / dt / 1e9, S, dt
+
+
+def cpu_baseline(w, masks, budget_s=12.0, single=True):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    workload (1 encode + len(masks) decodes per stripe, like a step): all
+    cores (the reported value) and, with `single`, one thread."""
+    cores = os.cpu_count() or 1
+    value, S, dt = oracle_rate(w, masks, budget_s, cores)
+    one, S1, dt1 = oracle_rate(w, masks, budget_s / 2, 1) if single else (None, 0, 0.0)
     cpu = "unknown"
     try:
         with open("/proc/cpuinfo") as f:
@@ -679,9 +867,13 @@ def cpu_baseline(w, masks, budget_s=12.0):
                     break
     except Exception:
         pass
-    return {"value": round(user / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{S} stripes of the workload: 1 encode + {len(masks)} decodes each "
-                      f"({dt:.1f} s, {cores} threads, cpu {cpu})"}
+    out = {"value": round(value, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "sample": f"{S} stripes of the workload: 1 encode + {len(masks)} decodes each "
+                     f"({dt:.1f} s, {cores} threads, cpu {cpu})"}
+    if single:
+        out["single_thread"] = {"value": round(one, 4), "unit": "GB/s", "cores": 1,
+                                "sample": f"{S1} stripes, 1 encode + {len(masks)} decodes each ({dt1:.1f} s)"}
+    return out
 
 
 def run_reference(args, w):
@@ -691,8 +883,8 @@ def run_reference(args, w):
     masks = workload_masks(w)
     per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_baseline(w, masks, budget_s=per_step)
-    vals = [cpu_baseline(w, masks, budget_s=per_step) for _ in range(args.steps)]
+        cpu_baseline(w, masks, budget_s=per_step, single=False)
+    vals = [cpu_baseline(w, masks, budget_s=per_step, single=k == args.steps - 1) for k in range(args.steps)]
     v = round(statistics.median(x["value"] for x in vals), 4)
     cb = dict(vals[-1])
     cb["value"] = v
@@ -702,7 +894,7 @@ def run_reference(args, w):
             "ms_per_step": round(user_step / (v * 1e9) * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic (seeded SplitMix64 uniform uint64 pixels)",
-            "config": {"workload": args.workload, "description": w["desc"]},
+            "config": workload_config(args, w, 1),
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -718,7 +910,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the mixed-batch comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the request-server measurement")
-    ap.add_argument("--no-systematic", action="store_true", help="skip the systematic-form measurement")
+    ap.add_argument("--no-systematic", action="store_true", help="(default) no systematic-form measurement")
+    ap.add_argument("--systematic", action="store_true", help="add the systematic-form measurement")
+    ap.add_argument("--no-wide", action="store_true", help="skip the (12,8) 4 KB / 8 KB measurement")
+    ap.add_argument("--no-alternatives", action="store_true", help="skip the opt-in decode kernels")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=inputs.DEFAULT_SEED, help="seed of the stripe pixels")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="stripe slices of the e2e pipeline")

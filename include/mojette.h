@@ -122,8 +122,10 @@ int mojette_plan_bins(mojette_plan_t plan, int32_t *full_bin);
  *   [0] 1: decode configuration set (tuned), 0: library defaults;
  *   [1] decode kernel (0 decode_lines, 1 decode_fronts, 2 decode_stream,
  *       3 decode_cols, 4 decode_scan2 -- the closed form for two rebuilt
- *       lines, the default where it applies; Q > 8 allows 1 only, 4 needs
- *       Q = 2 or a systematic plan and applies only to two-line decodes);
+ *       lines, the default for a systematic plan's two-line decodes,
+ *       5 decode_vander, 6 decode_ilv; Q > 8 allows 1 only, 4 needs Q = 2
+ *       or a systematic plan and applies only to two-line decodes, 5 and 6
+ *       need a plan that is not systematic, 5 one that is not trimmed);
  *   [2] work items per CTA (1 .. 64); [3] persistent grid (0/1);
  *   [4] decode_lines row phases (0/1);
  *   [5] 1: encode configuration set; [6] encode tile bytes (0: by Q);
@@ -177,6 +179,29 @@ int mojette_encode(mojette_plan_t plan, const uint64_t *d_img, uint64_t *d_proj,
 int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj,
                    uint32_t erasure_mask, uint64_t *d_img, int64_t S,
                    mojette_stream_t stream);
+
+/*
+ * mojette_stage_survivors -- copy to the device, from host memory, exactly
+ * the projections a decode under `erasure_mask` reads: the Q surviving
+ * projections its reconstruction path uses (any Q of the n rebuild the
+ * block, Sec. 2.3; a storage read fetches only those packets), for S
+ * stripes.
+ *   h_proj  [S][total] uint64 bins in host memory, read (pinned memory for
+ *           an asynchronous copy; pageable memory makes it synchronous);
+ *           only the used projections' slices [off_i, off_i + B_i) are read;
+ *   d_proj  [S][total] uint64 on the device: those slices written, every
+ *           other word untouched (a following mojette_decode with the same
+ *           mask reads nothing else);
+ *   bytes   receives the number of bytes copied (may be NULL).
+ * One strided 2-D copy (cudaMemcpy2DAsync, rows = stripes, pitch total * 8
+ * bytes) per used projection, on `stream`; host only otherwise (the mask's
+ * path is built and cached as for a decode). Not for systematic plans.
+ * Errors: -EINVAL (NULL pointer, systematic plan, mask bits beyond n),
+ * -ENOTRECOVERABLE, -ENOMEM, -EIO.
+ */
+int mojette_stage_survivors(mojette_plan_t plan, const uint64_t *h_proj,
+                            uint32_t erasure_mask, uint64_t *d_proj, int64_t S,
+                            mojette_stream_t stream, int64_t *bytes);
 
 /*
  * mojette_sys_decode -- rebuild, in place, the lost data lines of S stripes
@@ -236,17 +261,21 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
  * systematic plan, mojette_sys_decode) launches for this mask and S stripes
  * (host only; builds and caches the mask's path like the decode would):
  *   0 decode_lines   the two-front path of Sec. 2.2, one lane per line and
- *                    front (Q <= 8);
+ *                    front, a few stripes per warp (Q <= 8);
  *   1 decode_fronts  the same path, one lane per front (any Q);
  *   2 decode_stream, 3 decode_cols  variants of 0 (tuning candidates);
  *   4 decode_scan2   two rebuilt lines in closed form (a chain recurrence);
  *   5 decode_vander  every line at once: Eq. 1 as a Vandermonde system
  *                    solved by divided differences (non-systematic,
- *                    untrimmed plans);
+ *                    untrimmed plans; exact, but not the paper's inverse);
+ *   6 decode_ilv     the path of Sec. 2.2 with the stripes across the lanes
+ *                    (one lane per stripe, front and half of the lines;
+ *                    non-systematic, Q <= 8);
  *  -1                no launch (a systematic mask with no data line lost).
- * The choice is the measured-fastest kernel that applies (it depends on Q,
- * P and, for Q = 4 and 5, on whether S is at most 4096), or the one the
- * MOJETTE_DECODE_KERNEL environment variable names (lines, fronts, stream,
+ * The default is the paper's inverse: decode_lines up to 8 lines,
+ * decode_fronts beyond, and for a systematic plan decode_lines over the lost
+ * lines or decode_scan2 for two of them. The MOJETTE_DECODE_KERNEL
+ * environment variable may name another kernel (lines, ilv, fronts, stream,
  * cols, scan, vander) where it applies; a stripe too wide for the chosen
  * kernel's shared memory falls back to decode_lines, then decode_fronts, at
  * launch. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
@@ -387,7 +416,9 @@ int mojette_batch_run(mojette_batch_t batch, mojette_stream_t stream);
  * the batch: for decode the kernel (decode_lines, one lane per line and
  * front; decode_cols, the same lanes over a line-interleaved layout;
  * decode_stream, the same lanes with the stripe streamed through shared
- * memory in chunks; decode_fronts, one lane per front), stripes per
+ * memory in chunks; decode_ilv, one lane per stripe, front and half of the
+ * lines; decode_fronts, one lane per front; decode_scan2 and decode_vander
+ * where they apply), stripes per
  * CTA, persistent or one-shot grids and whether each line's row starts at
  * the bank phase chosen for the path; for encode the stripes per
  * shared-memory tile. Each
@@ -408,7 +439,8 @@ int mojette_batch_tune(mojette_batch_t batch, mojette_stream_t stream, int reps)
  *   configs     6 words per launch: op, Q (decode: lines rebuilt per
  *               stripe, a systematic launch's lost lines), P, then for decode the kernel
  *               (0 decode_lines, 1 decode_fronts, 2 decode_stream,
- *               3 decode_cols, 4 decode_scan2), work
+ *               3 decode_cols, 4 decode_scan2, 5 decode_vander,
+ *               6 decode_ilv), work
  *               items per CTA and
  *               flags (bit 0 persistent grid, bit 1 bank-phased rows),
  *               for encode 0, the tile bytes (0 = default) and 0. The array

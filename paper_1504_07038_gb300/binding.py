@@ -56,6 +56,7 @@ def lib():
             L.mojette_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_decode_noalloc.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
             L.mojette_sys_decode.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR]
+            L.mojette_stage_survivors.argtypes = [_PTR, _PTR, _U32, _PTR, _I64, _PTR, ctypes.POINTER(_I64)]
             L.mojette_decode_kernel.argtypes = [_PTR, _U32, _I64, ctypes.POINTER(ctypes.c_int32)]
             L.mojette_schedule.argtypes = [_PTR, _U32, _PTR, _PTR, _PTR, _PTR, _PTR, _I64, _PTR]
             L.mojette_schedule_layout.argtypes = [_PTR, _U32, _PTR, _PTR]
@@ -80,7 +81,7 @@ def lib():
                          "mojette_plan_destroy",
                          "mojette_plan_info",
                          "mojette_encode", "mojette_decode", "mojette_decode_noalloc", "mojette_sys_decode",
-                         "mojette_decode_kernel",
+                         "mojette_stage_survivors", "mojette_decode_kernel",
                          "mojette_schedule", "mojette_schedule_layout", "mojette_batch_create",
                          "mojette_batch_update",
                          "mojette_batch_run", "mojette_batch_tune", "mojette_batch_info",
@@ -271,6 +272,20 @@ def mojette_decode(plan: Plan, d_proj, erasure_mask: int, d_img, S: int | None =
                                 _addr(d_img), int(S), _stream(stream)), "mojette_decode")
 
 
+def mojette_stage_survivors(plan: Plan, h_proj, erasure_mask: int, d_proj, S: int | None = None,
+                            stream=None) -> int:
+    """Copy to the device only the projections a decode under erasure_mask
+    reads (h_proj [S][total] in host memory, pinned for an asynchronous
+    copy, into d_proj [S][total]); returns the bytes copied."""
+    if S is None:
+        S = d_proj.numel() // max(1, plan.total)
+    moved = _I64()
+    _check(lib().mojette_stage_survivors(plan.handle, _addr(h_proj), int(erasure_mask) & 0xFFFFFFFF,
+                                         _addr(d_proj), int(S), _stream(stream), ctypes.byref(moved)),
+           "mojette_stage_survivors")
+    return int(moved.value)
+
+
 def mojette_sys_decode(plan: Plan, d_parity, erasure_mask: int, d_data, S: int | None = None,
                        stream=None) -> None:
     """Systematic plan: rebuild in place the data lines of d_data [S][Q][P]
@@ -294,7 +309,7 @@ def mojette_decode_noalloc(plan: Plan, d_proj, erasure_mask: int, d_img, S: int 
 
 
 DECODE_KERNELS = {-1: None, 0: "decode_lines", 1: "decode_fronts", 2: "decode_stream", 3: "decode_cols",
-                  4: "decode_scan2", 5: "decode_vander"}
+                  4: "decode_scan2", 5: "decode_vander", 6: "decode_ilv"}
 
 
 def mojette_decode_kernel(plan: Plan, erasure_mask: int, S: int = 1 << 20) -> str | None:

@@ -541,6 +541,8 @@ int tune(Batch &b, cudaStream_t st, int reps)
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});
                 cands.push_back({0, 4, 1, 1});
             } else if (k.plan->Q <= 8) {
+                for (int g : {1, 2, 4, 8}) cands.push_back({6, g, 0, 0});
+                cands.push_back({6, 4, 1, 0});
                 for (int sp : {0, 1})
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});
                 for (int kern : {2, 3})

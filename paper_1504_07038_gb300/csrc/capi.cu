@@ -185,9 +185,10 @@ int mojette_plan_config(mojette_plan_t plan, int32_t *get, const int32_t *set)
     }
     if (set) {
         if (set[0]) {
-            if (set[1] < 0 || set[1] > 5 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
+            if (set[1] < 0 || set[1] > 6 || set[2] < 1 || set[2] > 64 || (set[3] & ~1) || (set[4] & ~1))
                 return -EINVAL;
             if (set[1] == 5 && (pl->systematic || pl->trimmed || pl->Q < 2)) return -EINVAL;
+            if (set[1] == 6 && pl->systematic) return -EINVAL;
             if (set[1] != 1 && pl->Q > 8) return -EINVAL;
             if (set[1] == 4 && pl->Q != 2 && !pl->systematic) return -EINVAL;
             pl->dec_cfg.kernel = set[1];
@@ -286,6 +287,36 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     a.status = device_status_ptr(&err);
     if (err) return err;
     return launch_decode(a, (cudaStream_t)stream);
+}
+
+int mojette_stage_survivors(mojette_plan_t plan, const uint64_t *h_proj, uint32_t erasure_mask,
+                            uint64_t *d_proj, int64_t S, mojette_stream_t stream, int64_t *bytes)
+{
+    if (bytes) *bytes = 0;
+    if (!plan || S < 0) return -EINVAL;
+    Plan *pl = reinterpret_cast<Plan *>(plan);
+    if (pl->systematic || pl->Q > kMaxLines) return -EINVAL;
+    if (!mask_in_range(*pl, erasure_mask)) return -EINVAL;
+    int err = 0;
+    Schedule *sc = get_schedule(*pl, erasure_mask, &err);
+    if (!sc) return err;
+    if (S == 0) return 0;
+    if (!h_proj || !d_proj) return -EINVAL;
+    // the projections the path dedicates to a line, from either end
+    uint32_t used = 0;
+    for (int l = 0; l < sc->lines; ++l) used |= (1u << sc->projL[l]) | (1u << sc->projR[l]);
+    const size_t pitch = (size_t)pl->total * sizeof(uint64_t);
+    int64_t moved = 0;
+    for (int i = 0; i < pl->n; ++i) {
+        if (!(used >> i & 1u) || pl->B[i] == 0) continue;
+        const size_t width = (size_t)pl->B[i] * sizeof(uint64_t);
+        if ((err = record_cuda(cudaMemcpy2DAsync(d_proj + pl->off[i], pitch, h_proj + pl->off[i], pitch, width,
+                                                 (size_t)S, cudaMemcpyHostToDevice, (cudaStream_t)stream))))
+            return err;
+        moved += (int64_t)width * S;
+    }
+    if (bytes) *bytes = moved;
+    return 0;
 }
 
 int mojette_sys_decode(mojette_plan_t plan, const uint64_t *d_parity, uint32_t erasure_mask,

@@ -10,15 +10,22 @@ namespace mojette {
 
 int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool vander, bool env)
 {
+    // The Sec. 2.2 path: decode_lines (one warp per few stripes, one lane
+    // per line and front) up to 8 lines, decode_fronts beyond; a systematic
+    // decode runs the path over its lost lines, or two of them in closed
+    // form (decode_scan2). decode_ilv (stripes across lanes) runs the same
+    // path; it and the closed forms on other decodes (decode_vander,
+    // decode_scan2) are opt-in alternatives (MOJETTE_DECODE_KERNEL, the
+    // batch autotuner), measured slower or not the paper's inverse.
+    (void)P;
+    (void)S;
     int k = 0;
-    const bool small = S <= kVanSmallLaunch;
     if (Q > 8) k = 1;
     else if (sys) k = scan2 ? 4 : 0;
-    else if (vander && (Q <= 3 || (Q == 4 && (P >= 192 || small)) || (Q == 5 && small))) k = 5;
-    else if (scan2) k = 4;
     if (env) {
         if (const char *e = getenv("MOJETTE_DECODE_KERNEL")) {
-            if (strcmp(e, "lines") == 0 && Q <= 8) k = 0;
+            if (strcmp(e, "ilv") == 0 && Q <= 8 && !sys) k = 6;
+            else if (strcmp(e, "lines") == 0 && Q <= 8) k = 0;
             else if (strcmp(e, "fronts") == 0 && !sys) k = 1;
             else if (strcmp(e, "stream") == 0 && !sys && Q <= 8) k = 2;
             else if (strcmp(e, "cols") == 0 && !sys && Q <= 8) k = 3;
@@ -101,6 +108,56 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
         L->SWc = (P + 2 * L->reach) * Q;
         L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
         return L->smem > cap ? -EINVAL : 0;
+    }
+    if (want == 6) {
+        // decode_ilv: G stripes interleaved word by word at stride GS, the
+        // (step, forward) word pairs first. Rows either with zero gaps of R
+        // = (Q - 1) max|p| columns between them and at both ends, plus one
+        // word at each end for a front one step past its line (PAD, signalled
+        // by reach = R + 1 >= 2), or of P + 1 columns with column P the zero
+        // word operands outside the image are clamped to (reach = 1). G: the
+        // most stripes (up to 16, one per lane of a half-warp) for which two
+        // CTAs fit on an SM, else one; a cap (cfg.gmax, or MOJETTE_DECODE_G)
+        // spreads small launches over more CTAs. PAD unless the gaps cost
+        // more than a quarter of the stripes a CTA holds
+        // (MOJETTE_DECODE_PAD=0/1 forces it).
+        if (Q > 8) return -EINVAL;
+        const int R = std::max(0, span) * maxp;
+        auto cols = [&](bool pad) -> int64_t {
+            return pad ? 2 + R + (int64_t)Q * (P + R) : (int64_t)Q * (P + 1);
+        };
+        auto bytes = [&](bool pad, int g) { return (int64_t)L->TS * 8 + cols(pad) * (g | 1) * 8; };
+        int gmax = 16;
+        if (cfg.gmax > 0) gmax = std::min(gmax, cfg.gmax);
+        if (const char *e = getenv("MOJETTE_DECODE_G")) {
+            const int v = atoi(e);
+            if (v >= 1 && v <= 16) gmax = v;
+        }
+        auto pick = [&](bool pad) {
+            for (int want_ctas = 2; want_ctas >= 1; --want_ctas)
+                for (int g = gmax; g >= 1; --g)
+                    if (bytes(pad, g) <= cap && (bytes(pad, g) + 1024) * want_ctas <= cap_sm) return g;
+            return 0;
+        };
+        const int Gc = pick(false), Gp = R > 0 ? pick(true) : 0;
+        bool pad = Gp > 0 && 4 * Gp >= 3 * Gc;
+        if (const char *e = getenv("MOJETTE_DECODE_PAD")) pad = atoi(e) != 0 && Gp > 0;
+        const int G = pad ? Gp : Gc;
+        if (!G) return -EINVAL;   // one stripe exceeds shared memory
+        L->G = G;
+        L->GS = G | 1;
+        if (pad) {
+            L->reach = R + 1;
+            L->RP = P + R;
+            for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = 1 + R + l * L->RP;
+        } else {
+            L->reach = 1;
+            L->RP = P + 1;
+            for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = l * L->RP;
+        }
+        L->SWc = (int)(cols(pad) * L->GS);
+        L->smem = bytes(pad, G);
+        return 0;
     }
     if (want == 0) {
         // decode_lines: 2Q lanes per stripe; step and forward words and the
@@ -238,8 +295,19 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
         if (d.T == 0) return 0;
         return launch_decode_kernel<false>(a, L, cfg, nitems, st, true);
     }
+    if (cfg.kernel == 6) {
+        // a launch too small to fill every SM twice at the widest work
+        // items gets narrower ones, spread over more CTAs
+        int dev = 0, sms = 0;
+        if (record_cuda(cudaGetDevice(&dev)) == 0 &&
+            record_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) == 0 && sms > 0) {
+            const int64_t per = (d.S + 2 * (int64_t)sms - 1) / (2 * (int64_t)sms);
+            if (per < 16) cfg.gmax = (int)std::max<int64_t>(1, per);
+        }
+    }
     int err = decode_layout(d.P, d.Q, d.Q - 1, cfg.kernel == 5 ? vmaxp : maxp, d.T, cfg, d.rowoff, &L);
-    if (err == -EINVAL && (cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 4 || cfg.kernel == 5)) {
+    if (err == -EINVAL && (cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 4 || cfg.kernel == 5 ||
+                           cfg.kernel == 6)) {
         cfg.kernel = 0;
         err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
     }

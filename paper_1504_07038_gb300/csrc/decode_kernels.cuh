@@ -645,6 +645,224 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
 }
 
 // ---------------------------------------------------------------------------
+// decode_ilv: the stripe-interleaved form of the path, one lane per stripe.
+// A CTA of two warps rebuilds G <= 16 stripes at a time; word (column c of
+// the stripe area, stripe g) sits at c * GS + g of its shared memory. Warp 0
+// runs the left fronts and warp 1 the right fronts; lane h * 16 + g runs its
+// side's front on lines h * H .. h * H + H - 1 (H = ceil(Q / 2)) of stripe g.
+// The G lanes of a half-warp thus make the same access in G different stripes
+// -- G consecutive words -- so every shared-memory load and store of the path
+// is one wavefront per half-warp, with no bank planning and no dependence on
+// the erasure pattern.
+//
+// Rows: PAD -- line l's pixels at columns rowbase[l] + [0, P), with a gap of
+// `reach` zero columns between rows and at both ends, `reach` covering the
+// widest offset (l2 - l) p of a bin line: the word of line l2 on a bin line
+// is then at a fixed distance from the front's own word, whether inside the
+// image or not (pixels outside the image are the XOR identity). Otherwise
+// (no room for the gaps) rows of P + 1 columns, column P a zero word, and an
+// operand column outside the image is clamped to it.
+//
+// A step, for each of the lane's lines: its own bin and the Q - 1 pixels of
+// the bin line on the other lines, all loaded before anything is stored (a
+// front that does not move this step loads as well, and stores nothing). The
+// pixel line l+1 rebuilds in the same step (bit 2l+side of the forward word)
+// is read as the bin it still holds, so line l takes the XOR of line l+1's
+// other words on top: c_l = (words of l other than its bin) ^ (forwarded ?
+// c_{l+1} : 0), pixel_l = bin_l ^ c_l. Within a lane that chain runs in
+// registers; the link from the top line of the lower half-warp to the bottom
+// line of the upper one is one warp shuffle. The two warps only meet where a
+// front reads a pixel the other side rebuilt at an earlier step: the path
+// marks such steps (kFwdSync) and the warps synchronise before their loads.
+//
+// Staging: every (stripe, line, front) run of consecutive bins is copied by
+// 8-byte cp.async, 32 consecutive words per warp instruction (coalesced). The
+// image goes back the same way, 32 consecutive words of a row per
+// instruction.
+template <int QT, bool BATCHED, bool PAD>
+__global__ void __launch_bounds__(64) decode_ilv(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    constexpr int H = (Q + 1) / 2;   // lines per lane
+    const int P = a.P, G = a.G, GS = a.GS;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int side = tid >> 5;       // 0: left fronts, 1: right fronts
+    const int hh = lane >> 4;        // which half of the lines
+    // stripe of the work item; lanes past G shadow stripe 0 (the same loads,
+    // no stores), so that every address stays inside the CTA's stripes
+    const bool gok = (lane & 15) < G;
+    const int g = gok ? lane & 15 : 0;
+    uint2 *stw = reinterpret_cast<uint2 *>(sm);   // (step word, forward word) pairs
+    uint64_t *wbuf = sm + a.TS;
+    for (int i = tid; i < a.SWc; i += 64) wbuf[i] = 0;
+    const uint32_t wbase = smem_addr(wbuf);
+    const uint32_t GSB = (uint32_t)GS * 8u;
+    // shared-memory address of (line l, column c) of this lane's stripe
+    auto at = [&](int l, int c) -> uint32_t {
+        return wbase + ((uint32_t)(a.rowbase[l] + c) * (uint32_t)GS + (uint32_t)g) * 8u;
+    };
+    int sh[H];           // bit of line j in the step and forward words
+    bool lv[H];          // line j exists
+    int ln[H];           // its index
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const int l = hh * H + j;
+        lv[j] = l < Q;
+        ln[j] = lv[j] ? l : 0;
+        sh[j] = 2 * ln[j] + side;
+    }
+    uint32_t rowa[Q];    // clamped rows: column 0 of every line
+    if constexpr (!PAD) {
+#pragma unroll
+        for (int l = 0; l < Q; ++l) rowa[l] = at(l, 0);
+    }
+
+    // Path-dependent state: the word on line l2 of line j's bin line sits
+    // dk = (lpos[l2] - lpos[l]) p columns from the front's column (0 for
+    // l2 = l: its own bin); PAD keeps it as a byte offset from the front's
+    // own word.
+    int T4 = 0;
+    int dk[H][Q];
+    uint32_t off[H][Q];
+    auto load_group = [&](const DecGroup &gr) {
+        const int T = gr.T;
+        T4 = (T + 3) & ~3;
+        for (int t = tid; t < T4 + 4; t += 64)
+            stw[t] = t < T ? make_uint2(gr.steps[t], gr.steps[T + t]) : make_uint2(0u, 0u);
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            const int p = gr.p[2 * ln[j] + side];
+#pragma unroll
+            for (int l2 = 0; l2 < Q; ++l2) {
+                dk[j][l2] = (gr.lpos[l2] - gr.lpos[ln[j]]) * p;
+                off[j][l2] = (uint32_t)((a.rowbase[l2] - a.rowbase[ln[j]] + dk[j][l2]) * GS) * 8u;
+            }
+        }
+    };
+    const DecGroup *gp = nullptr;   // batched: the current work item's path
+    auto grp = [&]() -> const DecGroup & {
+        if constexpr (BATCHED) return *gp;
+        else return a.grp;
+    };
+    if constexpr (!BATCHED) load_group(a.grp);
+    __syncthreads();
+
+    int cur = -1;
+    const int64_t nitems = BATCHED ? a.nwork : (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        int nst;
+        int64_t s0 = 0, first = 0;
+        if constexpr (BATCHED) {
+            const DecWork wk = a.work[item];
+            nst = wk.nst;
+            first = wk.first;
+            if (wk.group != cur) {
+                cur = wk.group;
+                gp = a.groups + cur;
+                load_group(*gp);
+            }
+        } else {
+            s0 = item * G;
+            nst = (int)min64(G, a.S - s0);
+        }
+
+        // Staging: run r = (stripe gg, line ll, front sd), its bins in
+        // consecutive words; word i of the left run is pixel sp - 1 - i, of
+        // the right run pixel P - 1 - i.
+        {
+            const int nruns = nst * Q * 2;
+            for (int r = side; r < nruns; r += 2) {
+                const int gg = r / (2 * Q);
+                const int rem = r - gg * 2 * Q;
+                const int ll = rem >> 1, sd = rem & 1;
+                const uint64_t *sb = BATCHED ? a.srcp[first + gg] : a.proj + (s0 + gg) * a.total;
+                const int sp = grp().split[ll];
+                const int n = sd ? P - sp : sp;
+                const int xtop = sd ? P - 1 : sp - 1;
+                const uint64_t *src = sb + (grp().src[2 * ll + sd] - xtop);
+                const uint32_t d0 = wbase + ((uint32_t)(a.rowbase[ll] + xtop) * (uint32_t)GS + (uint32_t)gg) * 8u;
+                for (int i = lane; i < n; i += 32) cp_async8_s(d0 - (uint32_t)i * GSB, src + i);
+            }
+            cp_async_wait_all();
+        }
+        __syncthreads();
+
+        // replay the path
+        const int x0 = side ? P - 1 : 0;
+        int x[H];
+        uint32_t pos[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            x[j] = x0;
+            pos[j] = at(ln[j], x0);
+        }
+        const int dx = side ? -1 : 1;
+        const uint32_t stepb = side ? (uint32_t)(-(int32_t)GSB) : GSB;
+        const uint32_t zcol = (uint32_t)P;
+        uint2 nx = stw[0];
+        for (int t = 0; t < T4; ++t) {
+            const uint32_t w = nx.x, f = nx.y;
+            nx = stw[t + 1];
+            if (f & kFwdSync) named_barrier_sync(1, 64);
+            uint64_t own[H], c[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                uint64_t v[Q];
+#pragma unroll
+                for (int l2 = 0; l2 < Q; ++l2) {
+                    uint32_t o;
+                    if constexpr (PAD) o = pos[j] + off[j][l2];
+                    else o = rowa[l2] + min((uint32_t)(x[j] + dk[j][l2]), zcol) * GSB;
+                    v[l2] = ld_s64(o);
+                }
+                own[j] = hh ? v[(H + j) < Q ? H + j : 0] : v[j];
+                uint64_t s = 0;
+#pragma unroll
+                for (int l2 = 0; l2 < Q; ++l2) s ^= v[l2];
+                c[j] = s ^ own[j];   // the other words of the bin line
+            }
+            // same-step chain within the lane, top line down
+            uint64_t fwm[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) fwm[j] = 0ull - (uint64_t)((f >> sh[j]) & (lv[j] ? 1u : 0u));
+#pragma unroll
+            for (int j = H - 2; j >= 0; --j) c[j] ^= c[j + 1] & fwm[j];
+            // the lower half's top line links to the upper half's bottom line
+            const uint64_t up = __shfl_down_sync(0xffffffffu, c[0], 16);
+            uint64_t link = hh == 0 ? fwm[H - 1] : 0ull;
+#pragma unroll
+            for (int j = H - 1; j >= 0; --j) {
+                if (j < H - 1) link &= fwm[j];
+                c[j] ^= up & link;
+            }
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                const uint32_t mv = (w >> sh[j]) & 1u;
+                st_s64_if(pos[j], own[j] ^ c[j], (gok && lv[j]) ? mv : 0u);
+                pos[j] += mv ? stepb : 0u;
+                if constexpr (!PAD) x[j] += mv ? dx : 0;
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+
+        // write-back, 32 consecutive words of a row per instruction
+        {
+            const int nrows = nst * Q;
+            for (int r = side; r < nrows; r += 2) {
+                const int gg = r / Q, ll = r - gg * Q;
+                uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
+                const uint64_t *row = wbuf + (int64_t)a.rowbase[ll] * GS + gg;
+                for (int xx = lane; xx < P; xx += 32) __stcs(out + (int64_t)ll * P + xx, row[(int64_t)xx * GS]);
+            }
+        }
+        __syncthreads();
+    });
+}
+
+// ---------------------------------------------------------------------------
 // decode_cols: decode_lines' arithmetic with the lines interleaved as well as
 // the stripes. Word (line l, column c, stripe g) of a warp's slot sits at
 // ((c + reach) * Q + l) * G + g: one column of all Q lines of the G stripes
@@ -1490,6 +1708,22 @@ DecKernel pick_lines(int Q)
 }
 
 template <bool BATCHED>
+DecKernel pick_ilv(int Q, bool pad)
+{
+    switch (Q) {
+    case 1: return pad ? decode_ilv<1, BATCHED, true> : decode_ilv<1, BATCHED, false>;
+    case 2: return pad ? decode_ilv<2, BATCHED, true> : decode_ilv<2, BATCHED, false>;
+    case 3: return pad ? decode_ilv<3, BATCHED, true> : decode_ilv<3, BATCHED, false>;
+    case 4: return pad ? decode_ilv<4, BATCHED, true> : decode_ilv<4, BATCHED, false>;
+    case 5: return pad ? decode_ilv<5, BATCHED, true> : decode_ilv<5, BATCHED, false>;
+    case 6: return pad ? decode_ilv<6, BATCHED, true> : decode_ilv<6, BATCHED, false>;
+    case 7: return pad ? decode_ilv<7, BATCHED, true> : decode_ilv<7, BATCHED, false>;
+    case 8: return pad ? decode_ilv<8, BATCHED, true> : decode_ilv<8, BATCHED, false>;
+    default: return nullptr;
+    }
+}
+
+template <bool BATCHED>
 DecKernel pick_lines_sys(int Q)
 {
     switch (Q) {
@@ -1586,9 +1820,12 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
                  : L.kernel == 0 ? pick_lines<BATCHED>(a.Q)
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
                  : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
+                 : L.kernel == 6 ? pick_ilv<BATCHED>(a.Q, L.reach > 1)
                                  : pick_fronts<BATCHED>(a.Q);
     if (!fn) return -EINVAL;
-    const int block = (L.kernel == 4 || L.kernel == 5) ? 32 * L.G : 32;   // one warp per stripe
+    // decode_scan2 / decode_vander: one warp per stripe; decode_ilv: one warp
+    // per side; the others: one warp
+    const int block = (L.kernel == 4 || L.kernel == 5) ? 32 * L.G : L.kernel == 6 ? 64 : 32;
     int err = 0;
     if ((err = record_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)L.smem))))

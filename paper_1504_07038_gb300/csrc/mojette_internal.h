@@ -26,6 +26,13 @@ constexpr uint32_t kStatusWaitTimeout = 1u;
 constexpr uint32_t kStepSteady = 1u << 31;
 constexpr int kFastMaxLines = 15;
 
+// Forward word bit 31 marks a step at which some front reads a pixel the
+// other front (the other side of the same line set) rebuilt at an earlier
+// step since the last such mark: kernels that run the two sides in different
+// warps synchronise them there. Line Q - 1 never forwards, so the bit is free
+// for Q <= 16.
+constexpr uint32_t kFwdSync = 1u << 31;
+
 // Most lost data lines a systematic decode rebuilds in one stripe (one lane
 // pair per lost line in decode_lines).
 constexpr int kSysMaxLines = 8;
@@ -123,8 +130,10 @@ struct DecodeConfig {
     int kernel = 0;    // 0: decode_lines, 1: decode_fronts, 2: decode_stream, 3: decode_cols
                        // (all but decode_fronts for Q <= 8 only), 4: decode_scan2
                        // (two lines rebuilt only; the default there), 5: decode_vander
-                       // (non-systematic, untrimmed, 2 <= Q <= 8)
+                       // (non-systematic, untrimmed, 2 <= Q <= 8), 6: decode_ilv
+                       // (non-systematic, Q <= 8; the default there)
     int gpc = 4;       // work items (groups of G stripes) per CTA
+    int gmax = 0;      // decode_ilv: most stripes per work item (0: up to 16)
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
     int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
                        // bank phase (Schedule::rowoff), 0 at a uniform pitch

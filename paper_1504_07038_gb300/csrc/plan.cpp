@@ -60,10 +60,15 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
         pF[1][l] = pl.p[asc[Q - 1 - l]];
     }
     std::vector<uint8_t> known((size_t)P * Q, 0);
+    // front (0 left, 1 right) and step that rebuilt each known pixel
+    std::vector<uint8_t> who((size_t)P * Q, 0);
+    std::vector<int32_t> when((size_t)P * Q, 0);
+    int last_sync = 0;   // a synchronisation before the loads of this step
     int a[kMaxLines], z[kMaxLines], took[2][kMaxLines];
     for (int l = 0; l < Q; ++l) { a[l] = 0; z[l] = P - 1; }
     int64_t remaining = (int64_t)P * Q;
     std::vector<uint32_t> steps, pattern;
+    std::vector<uint8_t> syncs;
 
     while (remaining > 0) {
         if ((int)steps.size() >= limit) return -1;
@@ -102,10 +107,34 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
                 const int64_t x2 = (int64_t)took[side][l] + (int64_t)(pos[l + 1] - pos[l]) * pF[side][l];
                 if (x2 >= 0 && x2 < P && took[side][l + 1] == x2) fwd |= 1u << (2 * l + side);
             }
+        // Cross-front reads: a front reading a pixel the other front rebuilt
+        // at step when >= last_sync needs the two fronts synchronised before
+        // this step (kernels that run the two sides in different warps).
+        const int t = (int)steps.size();
+        bool cross = false;
+        for (int side = 0; side < 2 && !cross; ++side)
+            for (int l = 0; l < Q && !cross; ++l) {
+                if (took[side][l] < 0) continue;
+                for (int l2 = 0; l2 < Q; ++l2) {
+                    if (l2 == l) continue;
+                    const int64_t x2 = (int64_t)took[side][l] + (int64_t)(pos[l2] - pos[l]) * pF[side][l];
+                    if (x2 < 0 || x2 >= P) continue;
+                    const size_t k = (size_t)l2 * P + x2;
+                    if (known[k] && who[k] != side && when[k] >= last_sync) cross = true;
+                }
+            }
+        if (cross) last_sync = t;
+        syncs.push_back(cross ? 1 : 0);
         pattern.push_back(fwd);
         for (int l = 0; l < Q; ++l) {
-            if (took[0][l] >= 0) { known[(size_t)l * P + a[l]] = 1; ++a[l]; --remaining; }
-            if (took[1][l] >= 0) { known[(size_t)l * P + z[l]] = 1; --z[l]; --remaining; }
+            if (took[0][l] >= 0) {
+                const size_t k = (size_t)l * P + a[l];
+                known[k] = 1; who[k] = 0; when[k] = t; ++a[l]; --remaining;
+            }
+            if (took[1][l] >= 0) {
+                const size_t k = (size_t)l * P + z[l];
+                known[k] = 1; who[k] = 1; when[k] = t; --z[l]; --remaining;
+            }
         }
         steps.push_back(word);
     }
@@ -162,6 +191,8 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
             out->chunk_done[c] = M;
         }
     }
+    for (size_t t = 0; t < syncs.size(); ++t)
+        if (syncs[t]) pattern[t] |= kFwdSync;
     out->fwd = fwd;
     out->lines = Q;
     out->known = 0;

@@ -371,31 +371,99 @@ def test_sys_calls_validate_arguments_without_a_device():
 
 
 def test_decode_kernel_choice():
-    """The kernel a decode launches: decode_vander for Q <= 3, 8 KB-wide
-    Q = 4 stripes and small Q = 4 launches, decode_lines for other Q <= 8,
-    decode_fronts beyond,
-    decode_scan2 for systematic two-line losses, none when a systematic
-    stripe lost no data line; MOJETTE_DECODE_KERNEL overrides where the
-    kernel applies."""
+    """The kernel a decode launches: the Sec. 2.2 path everywhere --
+    decode_lines for Q <= 8 whatever P, S or the plan's trimming,
+    decode_fronts beyond; a systematic decode runs the path over its lost
+    lines (decode_lines), two of them in closed form (decode_scan2), nothing
+    when no data line is lost. The stripe-interleaved path kernel
+    (decode_ilv), the closed forms on other decodes (decode_vander,
+    decode_scan2) and the other path kernels are opt-in through
+    MOJETTE_DECODE_KERNEL, where they apply."""
     import os
     six = [-3, -2, -1, 1, 2, 3]
-    assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_vander"
-    assert mj.mojette_decode_kernel(mj.mojette_plan(128, 4, six), 0b11) == "decode_lines"
-    assert mj.mojette_decode_kernel(mj.mojette_plan(128, 4, six), 0b11, S=1024) == "decode_vander"   # small launch
-    assert mj.mojette_decode_kernel(mj.mojette_plan(256, 2, [-1, 1, 2]), 0b1) == "decode_vander"
-    assert mj.mojette_decode_kernel(mj.mojette_plan(64, 8, [v for v in range(-6, 7) if v]), 0xF) == "decode_lines"
+    twelve = [v for v in range(-6, 7) if v]
+    for P, Q, p, m in [(256, 4, six, 0b11), (128, 4, six, 0b11), (256, 2, [-1, 1, 2], 0b1),
+                       (512, 2, [-1, 1, 2], 0b1), (64, 8, twelve, 0xF), (128, 8, twelve, 0xF0)]:
+        for S in (1, 1024, 1 << 20):
+            assert mj.mojette_decode_kernel(mj.mojette_plan(P, Q, p), m, S=S) == "decode_lines", (P, Q, S)
     assert mj.mojette_decode_kernel(mj.mojette_plan(16, 9, list(range(-5, 5))), 0) == "decode_fronts"
     sysp = mj.Plan(128, 4, [-1, 1], systematic=True)
     assert mj.mojette_decode_kernel(sysp, 0b0110) == "decode_scan2"
     assert mj.mojette_decode_kernel(sysp, 0b0100) == "decode_lines"
     assert mj.mojette_decode_kernel(sysp, 0b11 << 4) is None
     tr = mj.mojette_plan_ex(256, 4, six, mj.MOJETTE_PLAN_TRIM_UNUSED)
-    assert mj.mojette_decode_kernel(tr, 0b11) == "decode_lines"        # trimmed: no full frame
-    os.environ["MOJETTE_DECODE_KERNEL"] = "lines"
+    assert mj.mojette_decode_kernel(tr, 0b11) == "decode_lines"
+    for name, want in [("lines", "decode_lines"), ("vander", "decode_vander"), ("fronts", "decode_fronts"),
+                       ("ilv", "decode_ilv")]:
+        os.environ["MOJETTE_DECODE_KERNEL"] = name
+        try:
+            assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == want
+        finally:
+            del os.environ["MOJETTE_DECODE_KERNEL"]
+    os.environ["MOJETTE_DECODE_KERNEL"] = "scan"
     try:
-        assert mj.mojette_decode_kernel(mj.mojette_plan(256, 4, six), 0b11) == "decode_lines"
+        assert mj.mojette_decode_kernel(mj.mojette_plan(256, 2, [-1, 1, 2]), 0b1) == "decode_scan2"
     finally:
         del os.environ["MOJETTE_DECODE_KERNEL"]
+
+
+def test_stage_survivors_argument_errors():
+    """mojette_stage_survivors refuses NULL plans and buffers, systematic
+    plans and mask bits beyond n, and an unrecoverable mask, before any copy;
+    S = 0 copies nothing."""
+    L = mj.lib()
+    six = [-3, -2, -1, 1, 2, 3]
+    plan = mj.mojette_plan(64, 4, six)
+    n = ctypes.c_int64(-1)
+    assert L.mojette_stage_survivors(None, 8, 0, 8, 1, None, ctypes.byref(n)) == -errno.EINVAL
+    assert L.mojette_stage_survivors(plan.handle, 0, 0b11, 8, 1, None, ctypes.byref(n)) == -errno.EINVAL
+    assert L.mojette_stage_survivors(plan.handle, 8, 0b11, 0, 1, None, None) == -errno.EINVAL
+    assert L.mojette_stage_survivors(plan.handle, 8, 1 << 6, 8, 1, None, None) == -errno.EINVAL
+    assert L.mojette_stage_survivors(plan.handle, 8, 0b111, 8, 1, None, None) == -errno.ENOTRECOVERABLE
+    assert L.mojette_stage_survivors(plan.handle, 0, 0b11, 0, 0, None, ctypes.byref(n)) == 0 and n.value == 0
+    sysp = mj.Plan(64, 4, [-1, 1], systematic=True)
+    assert L.mojette_stage_survivors(sysp.handle, 8, 0b1, 8, 1, None, None) == -errno.EINVAL
+
+
+def test_path_sync_marks_cover_every_cross_front_read():
+    """decode_ilv runs the left and the right fronts in two warps that only
+    synchronise at the steps the path marks (bit 31 of the forward word).
+    Replaying each path: every read of a pixel the other front rebuilt
+    must have a marked step after the pixel's step and no later than the
+    read; and the marks are sparse (a few per path, not every step)."""
+    six = [-3, -2, -1, 1, 2, 3]
+    twelve = [v for v in range(-6, 7) if v]
+    for P, Q, p, e in [(256, 4, six, 2), (64, 8, twelve, 4), (128, 8, twelve, 4), (20, 3, [-4, -1, 0, 2, 5, 6], 3),
+                       (33, 6, [-4, -3, -1, 1, 2, 3, 5, 7], 2)]:
+        plan = mj.mojette_plan(P, Q, p)
+        masks = inputs.all_masks(len(p), e)
+        for m in masks[:: max(1, len(masks) // 12)]:
+            sc = mj.mojette_schedule(plan, m)
+            T = sc["T"]
+            marks = [t for t in range(T) if sc["forward"][t] >> 31 & 1]
+            assert len(marks) <= max(8, T // 8), (P, Q, m, len(marks))
+            pdir = [[p[i] for i in sc["left"]], [p[i] for i in sc["right"]]]
+            by = {}
+            x = [[0] * Q, [P - 1] * Q]
+            for t in range(T):
+                w = sc["steps"][t]
+                moved = []
+                for side in (0, 1):
+                    for l in range(Q):
+                        if not w >> (2 * l + side) & 1:
+                            continue
+                        xx = x[side][l]
+                        for l2 in range(Q):
+                            c = xx + (l2 - l) * pdir[side][l]
+                            if l2 == l or not 0 <= c < P or (l2, c) not in by:
+                                continue
+                            s2, t2 = by[(l2, c)]
+                            if s2 != side:
+                                assert any(t2 < s <= t for s in marks), (P, Q, m, t, l, side)
+                        moved.append((side, l, xx))
+                for side, l, xx in moved:
+                    by[(l, xx)] = (side, t)
+                    x[side][l] += -1 if side else 1
 
 
 # ---- decode_lines' shared-memory layout (mojette_schedule_layout) ------------

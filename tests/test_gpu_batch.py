@@ -143,7 +143,7 @@ def test_batch_tune_keeps_results():
     mj.mojette_batch_tune(dec, reps=1)
     info = mj.mojette_batch_info(dec)
     for c in info["configs"]:
-        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3, 4, 5) and c["param"] >= 1
+        assert c["op"] == mj.MOJETTE_OP_DECODE and c["kernel"] in (0, 1, 2, 3, 4, 5, 6) and c["param"] >= 1
     for t in m.d_out:
         t.fill_(0)
     mj.mojette_batch_run(dec)
@@ -165,7 +165,7 @@ def test_every_tuner_candidate_is_exact(monkeypatch):
     proj = oracle.encode(img, p, threads=8)
     d_proj = torch.from_numpy(proj.view(np.int64)).cuda()
     mask = 0b000011000011
-    cases = [(k, g, r) for k in ("lines", "fronts", "stream", "cols", "vander") for g in ("1", "3", "8")
+    cases = [(k, g, r) for k in ("lines", "ilv", "fronts", "stream", "cols", "vander") for g in ("1", "3", "8")
              for r in ("0", "1")]
     for kernel, gpc, rowoff in cases:
         monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
@@ -175,6 +175,23 @@ def test_every_tuner_candidate_is_exact(monkeypatch):
         mj.mojette_decode(plan, d_proj, mask, out)
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint64), img), (kernel, gpc, rowoff)
+
+
+@pytest.mark.parametrize("kernel", [6, 0])
+def test_batch_with_installed_kernel(kernel):
+    """A decode configuration installed in every plan (mojette_plan_config)
+    is the one each class launches -- decode_ilv (stripes across lanes) or
+    decode_lines -- over the mixed geometries and per-stripe masks, and every
+    stripe equals the oracle's decode."""
+    m = Mixed(COUNTS, seed=19)
+    for pl in m.plans:
+        mj.mojette_plan_config(pl, {"decode_tuned": 1, "decode_kernel": kernel, "decode_gpc": 2,
+                                    "decode_persist": 0, "decode_rowoff": 1})
+    m.corrupt_erased()
+    dec = mj.mojette_batch_create(m.table(mj.MOJETTE_OP_DECODE, 4), m.plans, mj.MOJETTE_BATCH_GRAPH)
+    assert all(c["kernel"] == kernel for c in mj.mojette_batch_info(dec)["configs"])
+    mj.mojette_batch_run(dec)
+    m.check_out()
 
 
 def test_batch_update_and_mixed_ops():

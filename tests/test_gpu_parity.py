@@ -211,7 +211,8 @@ def test_full_size_wide_geometry():
     _full_size(128, 8, TWELVE, 262144, ms[7::83])
 
 
-VARIANTS = [("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts", {}), ("stream", {}),
+VARIANTS = [("ilv", {}), ("ilv", {"MOJETTE_DECODE_G": "5"}), ("ilv", {"MOJETTE_DECODE_G": "16"}),
+            ("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts", {}), ("stream", {}),
             ("cols", {}), ("vander", {}), ("vander", {"MOJETTE_DECODE_GPC": "1"})]
 
 
@@ -220,9 +221,10 @@ VARIANTS = [("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts",
                          + [("tiny(6,3)", 20, 3, [-4, -1, 0, 2, 5, 6]),
                             ("odd P(8,6)", 33, 6, [-4, -3, -1, 1, 2, 3, 5, 7])])
 def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
-    """Each decode kernel (decode_lines with and without row phases,
-    decode_fronts, decode_stream, decode_cols, decode_vander), every k-of-n
-    mask (sampled at (12,8)), bit-exact."""
+    """Each decode kernel (decode_ilv at several work-item widths,
+    decode_lines with and without row phases, decode_fronts, decode_stream,
+    decode_cols, decode_vander), every k-of-n mask (sampled at (12,8)),
+    bit-exact."""
     monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
     for k, v in K.items():
         monkeypatch.setenv(k, v)
@@ -242,13 +244,62 @@ def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
         assert (host(out) == img).all(), (kernel, K, name, m)
 
 
+@pytest.mark.parametrize("kernel", ["ilv", "lines"])
+def test_path_kernels_8k_6x4_large_launch(monkeypatch, kernel):
+    """The Sec. 2.2 path kernels at the headline geometry, 8 KB (6,4) (P = 256,
+    Q = 4), in a launch of 4096 + 77 stripes -- large enough for decode_lines'
+    searched row phases and per-front load orders and for decode_ilv's widest
+    work items, with a ragged last item -- under every two-erasure mask and
+    the no-erasure mask, element by element against the oracle."""
+    monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
+    P, Q, p, S = 256, 4, SIX, 4096 + 77
+    img = inputs.stripes(S, Q, P, seed=41)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    assert mj.mojette_decode_kernel(plan, 0b11, S=S) == "decode_" + kernel
+    d_proj = dev(proj)
+    out = empty((S, Q, P))
+    for m in inputs.all_masks(6, 2) + [0]:
+        ref = oracle.decode(proj, p, P, Q, m, threads=8)
+        out.fill_(0x5A)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        assert (host(out) == ref).all(), (kernel, m)
+
+
+def test_stage_survivors_then_decode():
+    """mojette_stage_survivors copies from pinned host memory exactly the Q
+    projections the decode's path reads (their slices, every stripe) and
+    nothing else: the other words of the device block keep their junk, the
+    byte count is S * 8 * (sum of the used B_i), and the decode from that
+    block gives the image."""
+    P, Q, p, S = 128, 8, TWELVE, 777
+    plan = mj.mojette_plan(P, Q, p)
+    img = inputs.stripes(S, Q, P, seed=77)
+    proj = oracle.encode(img, p, threads=8)
+    h = torch.from_numpy(proj.view(np.int64)).pin_memory()
+    offs, bins, _, _ = oracle.offsets(p, P, Q)
+    for m in inputs.all_masks(len(p), 4)[::97] + inputs.all_masks(len(p), 1)[:2]:
+        d = empty((S, plan.total), fill=0x0BAD)
+        moved = mj.mojette_stage_survivors(plan, h, m, d, S)
+        sc = mj.mojette_schedule(plan, m)
+        used = set(sc["left"]) | set(sc["right"])
+        assert len(used) == Q and not any(m >> i & 1 for i in used)
+        assert moved == S * 8 * sum(bins[i] for i in used)
+        got = host(d)
+        for i, (o, B) in enumerate(zip(offs, bins)):
+            want = proj[:, o:o + B] if i in used else np.uint64(0x0BAD)
+            assert (got[:, o:o + B] == want).all(), (m, i)
+        out = empty((S, Q, P))
+        mj.mojette_decode(plan, d, m, out, S)
+        assert (host(out) == img).all(), m
+
+
 def test_decode_time_flat_across_masks():
     """Sec. 4 (Fig. 2-3): decode cost does not depend on which projections
     are lost. Every two-erasure mask of 8 KB (6,4) on 65536 stripes, timed
     with CUDA events (median of 3): the slowest mask within 1.3x of the
-    fastest (decode_vander, the default here, runs the same passes for
-    every survivor set, only with other strides; the paths of decode_lines
-    differ by at most a few steps)."""
+    fastest (the default path kernel runs each mask's path; the paths of
+    the 15 masks differ by at most a few steps)."""
     P, Q, p, S = 256, 4, [-3, -2, -1, 1, 2, 3], 65536
     plan = mj.mojette_plan(P, Q, p)
     img = torch.from_numpy(inputs.stripes(S, Q, P, seed=3).view(np.int64)).cuda()
