@@ -4,9 +4,11 @@ The no-allocation entry point serves callers that cannot call cudaMalloc --
 for instance a storage server whose device memory all belongs to its own
 buffer pool, or a request path that must not take cudaMalloc's device-wide
 synchronisation. It keeps the reconstruction path in a fixed scratch array
-inside the library. Two calls in a row, on different geometries and erasure
-masks (the second overwrites the scratch the first used), must each give
-exactly what mojette_decode gives on the same inputs.
+inside the library. Calls in a row, on different geometries and erasure
+masks whose paths all run through that scratch (each overwrites what the
+previous one left there), must each give exactly what mojette_decode gives
+on the same inputs; and a call allocates nothing on the device, even for a
+mask it has not seen before.
 """
 import errno
 
@@ -38,6 +40,10 @@ def test_noalloc_decode_matches_decode_on_two_calls_in_a_row():
 
     a = _case(mj, 256, 4, SIX, 1001, 0b100100, seed=21)
     b = _case(mj, 128, 8, TWELVE, 777, 0b010100100001, seed=22)
+    # both decodes follow a reconstruction path, read from the shared scratch
+    assert mj.mojette_decode_kernel(a[0], 0b100100, 1001) == "decode_lines"
+    assert mj.mojette_decode_kernel(b[0], 0b010100100001, 777) == "decode_lines"
+    assert mj.mojette_schedule(a[0], 0b100100)["T"] != mj.mojette_schedule(b[0], 0b010100100001)["T"]
     mj.mojette_decode_noalloc(a[0], a[2], 0b100100, a[4], 1001)
     mj.mojette_decode_noalloc(b[0], b[2], 0b010100100001, b[4], 777)
     torch.cuda.synchronize()
@@ -46,6 +52,27 @@ def test_noalloc_decode_matches_decode_on_two_calls_in_a_row():
         # bit-exact, the tolerance of every integer test here
         assert bool((got == want).all())
         assert bool((got == img).all())
+    # the first path again, after the second overwrote the scratch
+    a[4].fill_(3)
+    mj.mojette_decode_noalloc(a[0], a[2], 0b100100, a[4], 1001)
+    torch.cuda.synchronize()
+    assert bool((a[4] == a[3]).all())
+
+
+def test_noalloc_decode_allocates_no_device_memory():
+    from paper_1504_07038_gb300 import binding as mj
+
+    plan, img, proj, want, got = _case(mj, 128, 8, TWELVE, 513, 0b000011110000, seed=23)
+    mj.mojette_decode_noalloc(plan, proj, 0b000011110000, got, 513)   # set-up on this device
+    torch.cuda.synchronize()
+    fresh = 0b110000000011                                            # a mask not decoded before
+    free0 = torch.cuda.mem_get_info()[0]
+    mj.mojette_decode_noalloc(plan, proj, fresh, got, 513)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    mj.mojette_decode(plan, proj, fresh, want, 513)
+    torch.cuda.synchronize()
+    assert bool((got == want).all()) and bool((got == img).all())
 
 
 def test_noalloc_decode_refuses_an_oversized_schedule():
