@@ -531,11 +531,10 @@ int tune(Batch &b, cudaStream_t st, int reps)
             k.plan->tuned_enc = true;
         } else {
             struct Cand { int kernel, gpc, persist, rowoff; };
+            // the path kernels only: the closed forms (decode_scan2,
+            // decode_vander) are not the paper's inverse and run only when a
+            // configuration installed with mojette_plan_config names them
             std::vector<Cand> cands;
-            if (k.scan_ok)
-                for (int g : {1, 2, 4, 8}) cands.push_back({4, g, 0, 0});
-            if (k.van_ok)
-                for (int g : {1, 2, 4, 8}) cands.push_back({5, g, 0, 0});
             if (k.sys) {
                 for (int sp : {0, 1})
                     for (int g : {1, 2, 4, 8}) cands.push_back({0, g, 0, sp});

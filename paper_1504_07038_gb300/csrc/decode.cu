@@ -12,16 +12,15 @@ int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool van
 {
     // The Sec. 2.2 path: decode_lines (one warp per few stripes, one lane
     // per line and front) up to 8 lines, decode_fronts beyond; a systematic
-    // decode runs the path over its lost lines, or two of them in closed
-    // form (decode_scan2). decode_ilv (stripes across lanes) runs the same
-    // path; it and the closed forms on other decodes (decode_vander,
-    // decode_scan2) are opt-in alternatives (MOJETTE_DECODE_KERNEL, the
-    // batch autotuner), measured slower or not the paper's inverse.
+    // decode runs the path over its lost lines. decode_ilv (stripes across
+    // lanes) runs the same path; it (measured slower) and the closed forms
+    // (decode_scan2, decode_vander: exact, but not the paper's inverse) are
+    // opt-in alternatives (MOJETTE_DECODE_KERNEL, or a configuration
+    // installed with mojette_plan_config).
     (void)P;
     (void)S;
     int k = 0;
     if (Q > 8) k = 1;
-    else if (sys) k = scan2 ? 4 : 0;
     if (env) {
         if (const char *e = getenv("MOJETTE_DECODE_KERNEL")) {
             if (strcmp(e, "ilv") == 0 && Q <= 8 && !sys) k = 6;

@@ -374,11 +374,10 @@ def test_decode_kernel_choice():
     """The kernel a decode launches: the Sec. 2.2 path everywhere --
     decode_lines for Q <= 8 whatever P, S or the plan's trimming,
     decode_fronts beyond; a systematic decode runs the path over its lost
-    lines (decode_lines), two of them in closed form (decode_scan2), nothing
-    when no data line is lost. The stripe-interleaved path kernel
-    (decode_ilv), the closed forms on other decodes (decode_vander,
-    decode_scan2) and the other path kernels are opt-in through
-    MOJETTE_DECODE_KERNEL, where they apply."""
+    lines (decode_lines), nothing when no data line is lost. The
+    stripe-interleaved path kernel (decode_ilv), the closed forms
+    (decode_vander, decode_scan2) and the other path kernels are opt-in
+    through MOJETTE_DECODE_KERNEL, where they apply."""
     import os
     six = [-3, -2, -1, 1, 2, 3]
     twelve = [v for v in range(-6, 7) if v]
@@ -388,7 +387,7 @@ def test_decode_kernel_choice():
             assert mj.mojette_decode_kernel(mj.mojette_plan(P, Q, p), m, S=S) == "decode_lines", (P, Q, S)
     assert mj.mojette_decode_kernel(mj.mojette_plan(16, 9, list(range(-5, 5))), 0) == "decode_fronts"
     sysp = mj.Plan(128, 4, [-1, 1], systematic=True)
-    assert mj.mojette_decode_kernel(sysp, 0b0110) == "decode_scan2"
+    assert mj.mojette_decode_kernel(sysp, 0b0110) == "decode_lines"
     assert mj.mojette_decode_kernel(sysp, 0b0100) == "decode_lines"
     assert mj.mojette_decode_kernel(sysp, 0b11 << 4) is None
     tr = mj.mojette_plan_ex(256, 4, six, mj.MOJETTE_PLAN_TRIM_UNUSED)
@@ -403,6 +402,7 @@ def test_decode_kernel_choice():
     os.environ["MOJETTE_DECODE_KERNEL"] = "scan"
     try:
         assert mj.mojette_decode_kernel(mj.mojette_plan(256, 2, [-1, 1, 2]), 0b1) == "decode_scan2"
+        assert mj.mojette_decode_kernel(sysp, 0b0110) == "decode_scan2"
     finally:
         del os.environ["MOJETTE_DECODE_KERNEL"]
 

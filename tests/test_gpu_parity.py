@@ -436,10 +436,10 @@ TWO_LINE = [("4KB(3,2)", 256, 2, [-1, 1, 2]), ("8KB(3,2)", 512, 2, [-1, 1, 2]),
 @pytest.mark.parametrize("name,P,Q,p", TWO_LINE)
 @pytest.mark.parametrize("S", [1, 5, 4096 + 7])
 def test_two_line_closed_form(monkeypatch, kernel, name, P, Q, p, S):
-    """Two-line images decode by decode_scan2 (the chain recurrence of the two
-    dedicated projections, evaluated by pointer doubling) unless the sweep is
-    forced: every mask leaving >= 2 projections, ragged work items (4 stripes
-    per CTA), bit-exact with the oracle."""
+    """Two-line images: the default path kernel and, forced, decode_scan2
+    (the chain recurrence of the two dedicated projections, evaluated by
+    pointer doubling) and the sweep: every mask leaving >= 2 projections,
+    ragged work items, bit-exact with the oracle."""
     if kernel != "default":
         monkeypatch.setenv("MOJETTE_DECODE_KERNEL", kernel)
     n = len(p)

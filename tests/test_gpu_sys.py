@@ -107,9 +107,9 @@ def test_sys_decode_every_mask(name, P, Q, p):
 
 @pytest.mark.parametrize("name,P,Q,p", SYS_GEOMS)
 def test_sys_two_lost_lines_sweep_and_closed_form(monkeypatch, name, P, Q, p):
-    """Two lost data lines: decode_scan2 (the default) and the residual +
-    decode_lines sweep (forced) give the oracle's lines, for every pair of
-    lines and every surviving parity set."""
+    """Two lost data lines: the residual + decode_lines sweep (the default)
+    and decode_scan2 (the closed form, opt-in) give the oracle's lines, for
+    every pair of lines and every surviving parity set."""
     S = 67
     plan = mj.Plan(P, Q, p, systematic=True)
     img = inputs.stripes(S, Q, P, seed=5 * P + Q)
