@@ -309,7 +309,7 @@ def mojette_decode_noalloc(plan: Plan, d_proj, erasure_mask: int, d_img, S: int 
 
 
 DECODE_KERNELS = {-1: None, 0: "decode_lines", 1: "decode_fronts", 2: "decode_stream", 3: "decode_cols",
-                  4: "decode_scan2", 5: "decode_vander", 6: "decode_ilv"}
+                  4: "decode_scan2", 5: "decode_vander", 6: "decode_ilv", 7: "decode_ring"}
 
 
 def mojette_decode_kernel(plan: Plan, erasure_mask: int, S: int = 1 << 20) -> str | None:

@@ -74,6 +74,9 @@ static void fill_decode_args(const Plan &pl, const Schedule &sc, int64_t S, Deco
     a->vander = sc.vander;
     a->van_E0 = sc.van_E0;
     a->van_L = sc.van_L;
+    a->ring_R = sc.one_sided ? sc.ring_R : 0;
+    a->ring_D = sc.ring_D;
+    for (int l = 0; l < kMaxLines; ++l) a->ring_delta[l] = sc.ring_delta[l];
     for (int j = 0; j < kMaxLines; ++j) {
         a->van_q[j] = sc.van_q[j];
         a->van_base[j] = sc.van_base[j];
@@ -274,6 +277,12 @@ int mojette_decode(mojette_plan_t plan, const uint64_t *d_proj, uint32_t erasure
     if (S == 0) return 0;
     if (!d_img || !d_proj) return -EINVAL;
     if (!aligned16(d_img) || !aligned16(d_proj)) return -ERANGE;
+    // decode_ring runs the mask's one-sided path, where it fits a ring
+    if (choose_decode_kernel(pl->P, sc->lines, S, false, sc->scan2, sc->vander, true) == 7) {
+        int e2 = 0;
+        Schedule *rs = get_ring_schedule(*pl, erasure_mask, &e2);
+        if (rs && rs->ring_R > 0) sc = rs;
+    }
     uint32_t *dsteps = nullptr;
     if ((err = schedule_on_device(*pl, *sc, &dsteps))) return err;
     DecodeArgs a;
@@ -390,6 +399,11 @@ int mojette_decode_kernel(mojette_plan_t plan, uint32_t erasure_mask, int64_t S,
         return 0;
     }
     *kernel = choose_decode_kernel(pl->P, sc->lines, S, pl->systematic, sc->scan2, sc->vander, true);
+    if (*kernel == 7) {
+        int e2 = 0;
+        Schedule *rs = get_ring_schedule(*pl, erasure_mask, &e2);
+        if (!rs || rs->ring_R == 0 || pl->P % kRingChunk) *kernel = 0;   // no ring fits: decode_lines
+    }
     return 0;
 }
 

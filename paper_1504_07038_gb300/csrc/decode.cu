@@ -24,6 +24,7 @@ int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool van
     if (env) {
         if (const char *e = getenv("MOJETTE_DECODE_KERNEL")) {
             if (strcmp(e, "ilv") == 0 && Q <= 8 && !sys) k = 6;
+            else if (strcmp(e, "ring") == 0 && Q <= 8 && !sys) k = 7;
             else if (strcmp(e, "lines") == 0 && Q <= 8) k = 0;
             else if (strcmp(e, "fronts") == 0 && !sys) k = 1;
             else if (strcmp(e, "stream") == 0 && !sys && Q <= 8) k = 2;
@@ -106,6 +107,27 @@ int decode_layout(int P, int Q, int span, int maxp, int maxT, const DecodeConfig
         L->RP = 0;
         L->SWc = (P + 2 * L->reach) * Q;
         L->smem = (int64_t)L->TS * 8 + (int64_t)L->G * L->SWc * 8;
+        return L->smem > cap ? -EINVAL : 0;
+    }
+    if (want == 7) {
+        // decode_ring: one warp, G = 32 / Q stripes; the mbarriers (Q lines
+        // x R / 16 chunk slots), then each stripe's region of SWr words with
+        // line l's ring of R words at l * R; SWr = 2 mod 16 so that the G
+        // stripes' same slot falls in distinct bank pairs (G <= 8), regions
+        // and rings 16-byte aligned for the bulk copies. RP = R, reach = D
+        // (set by the caller, from the path; 0: no ring fits).
+        L->RP = cfg.ring_R;
+        L->reach = cfg.ring_D;
+        if (Q > 8 || L->RP < 2 * kRingChunk || L->RP % kRingChunk || P % kRingChunk) return -EINVAL;
+        L->G = std::max(1, 32 / Q);
+        L->GS = L->G;
+        const int NS = L->RP / kRingChunk;
+        L->SWc = (Q * NS + 1) & ~1;
+        for (int l = 0; l < kMaxLines; ++l) L->rowbase[l] = l * L->RP;
+        L->SWr = Q * L->RP;
+        while (L->SWr % 16 != 2) L->SWr += 2;
+        L->TS = 0;
+        L->smem = ((int64_t)L->SWc + (int64_t)L->G * L->SWr) * 8;
         return L->smem > cap ? -EINVAL : 0;
     }
     if (want == 6) {
@@ -304,9 +326,13 @@ int launch_decode(const DecodeArgs &d, cudaStream_t st)
             if (per < 16) cfg.gmax = (int)std::max<int64_t>(1, per);
         }
     }
+    if (cfg.kernel == 7 && (d.ring_R == 0 || d.P % kRingChunk)) cfg.kernel = 0;   // no ring for this path
+    cfg.ring_R = d.ring_R;
+    cfg.ring_D = d.ring_D;
+    for (int l = 0; l < kMaxLines; ++l) a.grp.ring_delta[l] = d.ring_delta[l];
     int err = decode_layout(d.P, d.Q, d.Q - 1, cfg.kernel == 5 ? vmaxp : maxp, d.T, cfg, d.rowoff, &L);
     if (err == -EINVAL && (cfg.kernel == 2 || cfg.kernel == 3 || cfg.kernel == 4 || cfg.kernel == 5 ||
-                           cfg.kernel == 6)) {
+                           cfg.kernel == 6 || cfg.kernel == 7)) {
         cfg.kernel = 0;
         err = decode_layout(d.P, d.Q, d.Q - 1, maxp, d.T, cfg, d.rowoff, &L);
     }

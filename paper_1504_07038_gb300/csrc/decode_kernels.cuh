@@ -886,6 +886,245 @@ __global__ void __launch_bounds__(64) decode_ilv(const __grid_constant__ DecPara
 }
 
 // ---------------------------------------------------------------------------
+// decode_ring: the path of Sec. 2.2 swept from the left end of every line
+// only (one front per line, the path built with split = P), each (stripe,
+// line) keeping a ring of R words of shared memory instead of its whole row:
+// for long lines the stripe's window -- the bins just ahead of the fronts
+// and the pixels the other lines still read just behind them -- is a small
+// part of the stripe, so several times more stripes fit on an SM.
+//
+// Lane = line * G + g (G = 32 / Q stripes per warp, one work item). Column c
+// of line l sits at ring slot R - 1 - ((c + delta_l) mod R), in the order of
+// the line's bins. Chunks of 16 columns (c + delta_l in [16 k, 16 k + 16))
+// are fetched D chunks ahead of the line's front by one 128-byte bulk copy
+// per (stripe, line) -- delta_l makes the chunk's bins 16-byte aligned --
+// completing on an mbarrier of the line's chunk slot; chunks overlapping
+// the image's ends take 8-byte cp.async copies for their in-image words and
+// zeros for the others, chunks outside the image zeros only, so a word
+// outside the image always reads 0 with no bounds test. A front entering
+// chunk k fetches chunk k + D and waits for chunk k. A 16-column chunk of
+// pixels is written back (all lanes, 128 consecutive bytes per half-warp)
+// after the step that rebuilds its last pixel. The host marks both events
+// in the path (Schedule::ringev) and replays the path under exactly these
+// rules before choosing this kernel: every read meets its bin, pixel or
+// zero, every pixel is still there when written back (ring_fits, plan.cpp).
+//
+// A step is decode_lines' step: own bin, the Q - 1 words of the bin line
+// (read even by a front that does not move: its slots are valid, its result
+// unused), the same-step chain over the lines by warp shuffles, the pixel
+// stored.
+template <int QT, bool BATCHED>
+__global__ void __launch_bounds__(32) decode_ring(const __grid_constant__ DecParams a)
+{
+    extern __shared__ __align__(16) uint64_t sm[];
+    constexpr int Q = QT;
+    constexpr int CH = kRingChunk;
+    const int P = a.P, G = a.G;
+    const int R = a.RP, D = a.reach, NS = a.RP / CH;
+    const uint32_t RM = (uint32_t)R - 1u;
+    const int lane = threadIdx.x & 31;
+    const int lq = lane / G;
+    const bool ok = lq < Q;
+    const int l = ok ? lq : 0;
+    const int g = ok ? lane - lq * G : 0;
+    // mbarriers (Q lines x NS chunk slots), then the stripes' regions of SWr
+    // words, line l2's ring at rowbase[l2] of its region
+    const uint32_t bar0 = smem_addr(sm);
+    const uint32_t rings = bar0 + (uint32_t)a.SWc * 8u;
+    const uint32_t rbase = rings + (uint32_t)g * (uint32_t)a.SWr * 8u;
+    if (lane == 0) {
+        for (int i = 0; i < Q * NS; ++i) mbar_init(bar0 + 8u * (uint32_t)i, (uint32_t)G);
+        mbar_init_fence();
+    }
+    __syncwarp();
+
+    const DecGroup &gr = a.grp;
+    const int p = gr.p[2 * l];
+    const int dl = gr.ring_delta[l];
+    // ring slot address of column c of the line whose ring starts at base,
+    // u = c + its delta
+    auto slot = [&](uint32_t base, int u) -> uint32_t { return base + ((~(uint32_t)u) & RM) * 8u; };
+    const uint32_t orb = rbase + (uint32_t)a.rowbase[l] * 8u;   // this lane's own ring
+    // the other lines of this lane's bin line, l + 1 + k (mod Q): ring and
+    // column offset (l2 - l) p + delta_l2 from the front's column
+    int eo[Q > 1 ? Q - 1 : 1];
+    uint32_t ro[Q > 1 ? Q - 1 : 1];
+#pragma unroll
+    for (int k = 0; k < Q - 1; ++k) {
+        const int l2 = (l + 1 + k) % Q;
+        eo[k] = (gr.lpos[l2] - gr.lpos[l]) * p + gr.ring_delta[l2];
+        ro[k] = rbase + (uint32_t)a.rowbase[l2] * 8u;
+    }
+    // steady steps: the links of the path's steady pattern (as decode_lines)
+    int chain = 0;
+    uint32_t slink[4] = {0u, 0u, 0u, 0u};
+    {
+        if (ok)
+            for (int j = l; j + 1 < Q && ((gr.fwd >> (2 * j)) & 1u); ++j) ++chain;
+        uint32_t c[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j)) & 1u : 0u;
+#pragma unroll
+        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+            uint32_t cl = 0;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                if (j == l) cl = c[j];
+            slink[r] = ok ? cl : 0u;
+            uint32_t nc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+        }
+    }
+    const int T = gr.T;
+    // (step, forward, event, 0) per step, from the next multiple of 4 words
+    // after the step and forward words; one zero entry after the last
+    const uint4 *sw4 = reinterpret_cast<const uint4 *>(gr.steps + ((2 * T + 3) & ~3));
+    uint32_t fpar = 0;   // bit s: phase parity of the latest fill of this line's chunk slot s
+    bool dead = false;
+
+    const int64_t nitems = (a.S + G - 1) / G;
+    for_items(a, nitems, [&](int64_t item) {
+        if (dead) return;
+        const int64_t s0 = item * G;
+        const int nst = (int)min64(G, a.S - s0);
+        const bool live = ok && g < nst;
+        const uint64_t *sb = a.proj + (s0 + g) * a.total;
+        const int64_t src = gr.src[2 * l];   // bin of column c at word src - c
+        // fill chunk k of this lane's ring: columns [16 k - dl, 16 k + 16 - dl)
+        auto fill = [&](int k) {
+            const int sl = k & (NS - 1);
+            const uint32_t bar = bar0 + 8u * (uint32_t)(l * NS + sl);
+            const int c0 = CH * k - dl;
+            // the chunk's slots: ascending addresses hold descending columns
+            const uint32_t dst = slot(orb, c0 + dl + CH - 1);
+            fpar ^= 1u << sl;
+            if (!ok) return;
+            const uint64_t *gs = sb + (src - (c0 + CH - 1));
+            if (live && c0 >= 0 && c0 + CH <= P && ((uintptr_t)gs & 15u) == 0) {
+                mbar_arrive_expect_tx(bar, CH * 8u);
+                tma_load_1d(dst, gs, CH * 8u, bar);
+            } else if (live && c0 + CH > 0 && c0 < P) {
+                for (int i = 0; i < CH; ++i) {
+                    const int c = c0 + CH - 1 - i;
+                    if (c >= 0 && c < P) cp_async8_s(dst + 8u * (uint32_t)i, sb + (src - c));
+                    else st_s64(dst + 8u * (uint32_t)i, 0ull);
+                }
+                cp_async_mbar_arrive(bar);
+            } else {
+                for (int i = 0; i < CH; ++i) st_s64(dst + 8u * (uint32_t)i, 0ull);
+                mbar_arrive(bar);
+            }
+        };
+        auto wait = [&](int k) -> bool {
+            const int sl = k & (NS - 1);
+            return !ok || mbar_wait_bounded(bar0 + 8u * (uint32_t)(l * NS + sl), (fpar >> sl & 1u) ^ 1u);
+        };
+        auto give_up = [&]() {
+            // a fetch did not land in time: report, let the copies still in
+            // flight land (bounded) before the CTA's shared memory goes away
+            if (lane == 0) atomicOr(a.status, kStatusWaitTimeout);
+            if (ok)
+                for (int sl = 0; sl < NS; ++sl)
+                    mbar_wait_bounded(bar0 + 8u * (uint32_t)(l * NS + sl), (fpar >> sl & 1u) ^ 1u);
+            dead = true;
+        };
+
+        // the previous item's accesses of the rings before the bulk writes
+        fence_proxy_async_smem();
+        __syncwarp();
+        for (int k = -1; k <= D; ++k) fill(k);
+        if (__any_sync(0xffffffffu, !wait(0))) {
+            give_up();
+            return;
+        }
+        __syncwarp();
+
+        int x = 0;
+        uint4 nx = sw4[0];
+        for (int t = 0; t < T; ++t) {
+            const uint32_t w = nx.x, f = nx.y, ev = nx.z;
+            nx = sw4[t + 1];
+            if (ev & 0xFFu) {
+                // fronts entering a chunk: fetch the one D ahead, wait for this one
+                fence_proxy_async_smem();
+                __syncwarp();
+                bool okk = true;
+                if (ok && (ev >> l & 1u)) {
+                    const int k = (x + dl) / CH;
+                    fill(k + D);
+                    okk = wait(k);
+                }
+                if (__any_sync(0xffffffffu, !okk)) {
+                    give_up();
+                    return;
+                }
+                __syncwarp();
+            }
+            const uint32_t at = slot(orb, x + dl);
+            const uint64_t own = ld_s64(at);
+            uint64_t lv[Q > 1 ? Q - 1 : 1];
+#pragma unroll
+            for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(slot(ro[k], x + eo[k]));
+            uint64_t v = 0;
+#pragma unroll
+            for (int k = 0; k < Q - 1; ++k) v ^= lv[k];
+            uint32_t act;
+            if (w & kStepSteady) {
+                act = ok ? 1u : 0u;
+                if constexpr (Q <= 4) {
+                    const uint64_t x0 = v;
+#pragma unroll
+                    for (int d = 1; d < Q; ++d) {
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x0, d * G);
+                        if (d <= chain) v ^= tv;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                        const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
+                        if (slink[r]) v ^= tv;
+                    }
+                }
+            } else {
+                act = ok ? (w >> (2 * l)) & 1u : 0u;
+                uint32_t c = (ok && act) ? (f >> (2 * l)) & 1u : 0u;
+#pragma unroll
+                for (int d = 1; d < Q; d <<= 1) {
+                    const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
+                    const uint32_t tc = __shfl_down_sync(0xffffffffu, c, d * G);
+                    if (c) {
+                        v ^= tv;
+                        c = tc;
+                    }
+                }
+            }
+            st_s64_if(at, own ^ v, act);
+            x += act ? 1 : 0;
+            __syncwarp();
+            if (ev >> 8) {
+                // write back the 16-column chunks just completed, a line at a time
+                uint32_t lines = (ev >> 8) & 0xFFu;
+                while (lines) {
+                    const int l2 = __ffs(lines) - 1;
+                    lines &= lines - 1;
+                    const int xc = __shfl_sync(0xffffffffu, x, l2 * G) - 1;   // the chunk's last column
+                    const int c = xc - (CH - 1) + (lane & (CH - 1));
+                    const int u2 = c + gr.ring_delta[l2];
+                    for (int gg = lane >> 4; gg < nst; gg += 2) {
+                        const uint32_t rg = rings + (uint32_t)gg * (uint32_t)a.SWr * 8u + (uint32_t)a.rowbase[l2] * 8u;
+                        __stcs(a.img + (s0 + gg) * (int64_t)Q * P + (int64_t)l2 * P + c, ld_s64(slot(rg, u2)));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    });
+}
+
+// ---------------------------------------------------------------------------
 // decode_cols: decode_lines' arithmetic with the lines interleaved as well as
 // the stripes. Word (line l, column c, stripe g) of a warp's slot sits at
 // ((c + reach) * Q + l) * G + g: one column of all Q lines of the G stripes
@@ -1747,6 +1986,26 @@ DecKernel pick_ilv(int Q, bool pad)
 }
 
 template <bool BATCHED>
+DecKernel pick_ring(int Q)
+{
+    if constexpr (BATCHED) {
+        return nullptr;   // plain launches only
+    } else {
+        switch (Q) {
+        case 1: return decode_ring<1, false>;
+        case 2: return decode_ring<2, false>;
+        case 3: return decode_ring<3, false>;
+        case 4: return decode_ring<4, false>;
+        case 5: return decode_ring<5, false>;
+        case 6: return decode_ring<6, false>;
+        case 7: return decode_ring<7, false>;
+        case 8: return decode_ring<8, false>;
+        default: return nullptr;
+        }
+    }
+}
+
+template <bool BATCHED>
 DecKernel pick_lines_sys(int Q)
 {
     switch (Q) {
@@ -1844,6 +2103,7 @@ int launch_decode_kernel(DecParams &a, const DecodeLayout &L, const DecodeConfig
                  : L.kernel == 2 ? pick_stream<BATCHED>(a.Q)
                  : L.kernel == 3 ? pick_cols<BATCHED>(a.Q)
                  : L.kernel == 6 ? pick_ilv<BATCHED>(a.Q, L.reach > 1)
+                 : L.kernel == 7 ? pick_ring<BATCHED>(a.Q)
                                  : pick_fronts<BATCHED>(a.Q);
     if (!fn) return -EINVAL;
     // decode_scan2 / decode_vander: one warp per stripe; decode_ilv: one warp

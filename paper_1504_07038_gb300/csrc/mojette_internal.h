@@ -121,8 +121,25 @@ struct Schedule {
     int32_t van_lo[kMaxLines] = {};
     int32_t van_hi[kMaxLines] = {};
     int32_t van_E0 = 0, van_L = 0;
+    // decode_ring: a one-sided path (left-to-right fronts only, split = P)
+    // replayed with a ring of ring_R words per (stripe, line) in shared
+    // memory, chunks of kRingChunk columns fetched ring_D chunks ahead of
+    // each line's front; line l's chunks start at columns 16k - ring_delta[l]
+    // (16-byte aligned sources). ring_R = 0: the path does not fit a ring.
+    bool one_sided = false;
+    int32_t ring_R = 0, ring_D = 0;
+    int32_t ring_delta[kMaxLines] = {};
+    // decode_ring events per step: bit l, line l's front enters a chunk
+    // (fetch chunk k + D, wait for chunk k); bit 8 + l, it completes the
+    // 16-column chunk its pixel ends (written back after the step). On the
+    // device the schedule then also holds (step, forward, event, 0) words
+    // per step, 16-byte aligned, after the step and forward words.
+    std::vector<uint32_t> ringev;
     std::map<int, uint32_t *> dev;   // device copy of `steps` then `fwdw`, per device
 };
+
+// decode_ring chunk width in columns (one 128-byte bulk copy).
+constexpr int kRingChunk = 16;
 
 // Launch configuration of the decode kernels (chosen by the autotuner for a
 // batch, else the defaults here).
@@ -131,9 +148,12 @@ struct DecodeConfig {
                        // (all but decode_fronts for Q <= 8 only), 4: decode_scan2
                        // (two lines rebuilt only; the default there), 5: decode_vander
                        // (non-systematic, untrimmed, 2 <= Q <= 8), 6: decode_ilv
-                       // (non-systematic, Q <= 8; the default there)
+                       // (non-systematic, Q <= 8), 7: decode_ring (non-systematic,
+                       // untrimmed, Q <= 8, a one-sided path that fits a ring)
     int gpc = 4;       // work items (groups of G stripes) per CTA
     int gmax = 0;      // decode_ilv: most stripes per work item (0: up to 16)
+    int ring_R = 0;    // decode_ring: ring words per (stripe, line), from the path
+    int ring_D = 0;    //   and chunks fetched ahead
     int persist = 0;   // 1: grid capped at the resident CTAs, grid-stride over items
     int rowoff = 1;    // decode_lines: 1 to start each line's row at the path's
                        // bank phase (Schedule::rowoff), 0 at a uniform pitch
@@ -166,6 +186,7 @@ struct Plan {
     std::map<int, int32_t *> full_bin_dev;   // device copy of full_bin, per device
     std::mutex mu;
     std::map<uint32_t, std::unique_ptr<Schedule>> schedules;
+    std::map<uint32_t, std::unique_ptr<Schedule>> ring_schedules;   // one-sided paths (decode_ring)
     // autotuned configurations (batch.cpp); used by batches of this plan
     bool tuned_dec = false, tuned_enc = false;
     DecodeConfig dec_cfg;
@@ -186,6 +207,9 @@ int choose_decode_kernel(int P, int Q, int64_t S, bool sys, bool scan2, bool van
 int build_schedule(const Plan &pl, uint32_t mask, Schedule *out);
 // Returns the cached schedule (building it on a miss) or sets *err.
 Schedule *get_schedule(Plan &pl, uint32_t mask, int *err);
+// The one-sided path of a mask for decode_ring (cached; ring_R = 0 when no
+// ring fits), or null with *err set (-EINVAL for systematic or trimmed plans).
+Schedule *get_ring_schedule(Plan &pl, uint32_t mask, int *err);
 // Unused-bin removal: keep in each projection only the bins some
 // reconstruction path reads, over every recoverable erasure mask.
 int trim_unused_bins(Plan &pl);
@@ -246,6 +270,8 @@ struct DecodeArgs {
     int32_t chunk_w, chunk_wait[kStreamChunks], chunk_done[kStreamChunks];
     int32_t rowoff[kMaxLines];
     uint32_t order[2 * kMaxLines];  // decode_lines load orders (see Schedule)
+    int32_t ring_R, ring_D;         // decode_ring (one-sided path): ring words, chunks ahead
+    int32_t ring_delta[kMaxLines];
     uint32_t *status;
 };
 int launch_decode(const DecodeArgs &a, cudaStream_t stream);
@@ -272,6 +298,7 @@ struct DecGroup {
     int32_t van_lo[kMaxLines];
     int32_t van_hi[kMaxLines];
     int32_t van_E0, van_L;
+    int32_t ring_delta[kMaxLines];  // decode_ring: chunk start shift of each line (see Schedule)
 };
 
 // One work item of a batched decode: nst (<= G) stripes of group `group`,

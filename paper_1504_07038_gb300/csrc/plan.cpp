@@ -22,6 +22,7 @@
 // replays it for every stripe that lost the same projections. Building it is
 // the paper's excluded pre-computation (Sec. 3.1).
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cerrno>
 #include <cstring>
@@ -51,9 +52,10 @@ namespace {
 // pos[1] < ... (all rows 0 .. Q-1 otherwise); the other pixel of a bin line
 // on line l2 is then (l2, x + (pos[l2] - pos[l]) p).
 int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines, int limit,
-          Schedule *out)
+          Schedule *out, bool one_sided = false)
 {
     const int P = pl.P, Q = lines;
+    const int sides = one_sided ? 1 : 2;
     int32_t pF[2][kMaxLines];
     for (int l = 0; l < Q; ++l) {
         pF[0][l] = pl.p[asc[l]];
@@ -72,8 +74,9 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
 
     while (remaining > 0) {
         if ((int)steps.size() >= limit) return -1;
+        for (int l = 0; l < Q; ++l) took[1][l] = -1;
         uint32_t word = 0;
-        for (int side = 0; side < 2; ++side) {
+        for (int side = 0; side < sides; ++side) {
             for (int l = Q - 1; l >= 0; --l) {
                 took[side][l] = -1;
                 if (a[l] > z[l]) continue;
@@ -141,7 +144,8 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
     // Steady steps: every front of every line moves and the operand pattern
     // is the schedule's most common one among such steps. The device runs
     // those with no per-line tests, forwarding exactly where `fwd` says.
-    const uint32_t all = Q >= 16 ? 0xFFFFFFFFu : (1u << (2 * Q)) - 1u;
+    uint32_t all = Q >= 16 ? 0xFFFFFFFFu : (1u << (2 * Q)) - 1u;
+    if (one_sided) all &= 0x55555555u;   // the left fronts only
     uint32_t fwd = 0;
     if (Q <= kFastMaxLines) {
         std::map<uint32_t, int> count;
@@ -575,6 +579,173 @@ int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
     return 0;
 }
 
+namespace {
+
+// Replays a one-sided path the way decode_ring runs it -- line l's ring of R
+// words holds column c at slot R - 1 - ((c + ring_delta[l]) mod R); at the
+// start chunks -1 .. D are filled (bins inside the image, zeros outside);
+// when a front enters chunk k (column c with c + ring_delta = 16 k > 0) it
+// fills chunk k + D over the slots of chunk k + D - R / 16; a chunk of 16
+// columns is written out at the end of the step that rebuilds its last
+// pixel -- and checks that every word a front reads holds what the path
+// needs at that moment: its own bin, the stale bin of a forwarded word, a
+// pixel rebuilt earlier, or a zero outside the image; and that every pixel
+// is still there when its chunk is written out.
+bool ring_fits(const Plan &pl, const Schedule &sc, int R, int D)
+{
+    const int P = pl.P, Q = sc.lines;
+    const int NS = R / kRingChunk;
+    if (Q < 1 || P % kRingChunk || R % kRingChunk || NS <= D + 1) return false;
+    struct Word {
+        int32_t col;
+        int8_t kind;   // 0 nothing, 1 bin, 2 pixel, 3 zero
+    };
+    std::vector<Word> ring((size_t)Q * R, Word{INT32_MIN, 0});
+    auto slot = [&](int l, int c) -> Word & {
+        const int u = ((c + sc.ring_delta[l]) % R + R) % R;
+        return ring[(size_t)l * R + (R - 1 - u)];
+    };
+    auto fill = [&](int l, int k) {
+        for (int i = 0; i < kRingChunk; ++i) {
+            const int c = kRingChunk * k + i - sc.ring_delta[l];
+            Word &w = slot(l, c);
+            w.col = c;
+            w.kind = (c >= 0 && c < P) ? 1 : 3;
+        }
+    };
+    for (int l = 0; l < Q; ++l)
+        for (int k = -1; k <= D; ++k) fill(l, k);
+    std::vector<int> x(Q, 0);
+    for (int t = 0; t < sc.T; ++t) {
+        const uint32_t w = sc.steps[(size_t)t], f = sc.fwdw[(size_t)t];
+        for (int l = 0; l < Q; ++l) {
+            if (!(w >> (2 * l) & 1u)) continue;
+            const int u = x[l] + sc.ring_delta[l];
+            if (u > 0 && u % kRingChunk == 0) fill(l, u / kRingChunk + D);
+        }
+        for (int l = 0; l < Q; ++l) {
+            if (!(w >> (2 * l) & 1u)) continue;
+            for (int l2 = 0; l2 < Q; ++l2) {
+                const int c = x[l] + (sc.lpos[l2] - sc.lpos[l]) * sc.pL[l];
+                const Word &o = slot(l2, c);
+                if (o.col != c) return false;
+                if (l2 == l || (l2 == l + 1 && (f >> (2 * l) & 1u))) {
+                    if (o.kind != 1) return false;   // own bin, or a forwarded word's stale bin
+                } else if (c < 0 || c >= P) {
+                    if (o.kind != 3) return false;
+                } else if (o.kind != 2) {
+                    return false;
+                }
+            }
+        }
+        for (int l = 0; l < Q; ++l) {
+            if (!(w >> (2 * l) & 1u)) continue;
+            Word &o = slot(l, x[l]);
+            o.kind = 2;
+            if (x[l] % kRingChunk == kRingChunk - 1)
+                for (int c = x[l] - (kRingChunk - 1); c <= x[l]; ++c) {
+                    const Word &q = slot(l, c);
+                    if (q.col != c || q.kind != 2) return false;
+                }
+            ++x[l];
+        }
+    }
+    for (int l = 0; l < Q; ++l)
+        if (x[l] != P) return false;
+    return true;
+}
+
+}  // namespace
+
+int build_ring_schedule(const Plan &pl, uint32_t mask, Schedule *out)
+{
+    if (pl.systematic || pl.trimmed || pl.Q > kMaxLines) return -EINVAL;
+    int pos[kMaxLines];
+    const int L = pl.Q;
+    for (int l = 0; l < L; ++l) pos[l] = l;
+    std::vector<int> surv;
+    for (int i = 0; i < pl.n; ++i)
+        if (!(mask >> i & 1u)) surv.push_back(i);
+    if ((int)surv.size() < L) return -ENOTRECOVERABLE;
+    std::stable_sort(surv.begin(), surv.end(), [&](int a, int b) {
+        return std::abs(pl.p[a]) < std::abs(pl.p[b]);
+    });
+    const int m = (int)surv.size();
+    std::vector<int> pick(L);
+    std::iota(pick.begin(), pick.end(), 0);
+    int best = -1, tried = 0;
+    Schedule tmp;
+    while (true) {
+        std::vector<int> asc(L);
+        for (int k = 0; k < L; ++k) asc[k] = surv[pick[k]];
+        std::sort(asc.begin(), asc.end(), [&](int a, int b) { return pl.p[a] < pl.p[b]; });
+        const int T = sweep(pl, asc, pos, L, best < 0 ? (1 << 30) : best, &tmp, true);
+        if (T >= 0 && (best < 0 || T < best)) {
+            best = T;
+            *out = tmp;
+        }
+        if (++tried >= kMaxCandidates) break;
+        int k = L - 1;
+        while (k >= 0 && pick[k] == m - L + k) --k;
+        if (k < 0) break;
+        ++pick[k];
+        for (int r = k + 1; r < L; ++r) pick[r] = pick[r - 1] + 1;
+    }
+    if (best < 0) return -ENOTRECOVERABLE;
+    out->mask = mask;
+    out->one_sided = true;
+    out->scan2 = out->vander = false;
+    // chunk starts: a chunk's bins are 16 consecutive words ending at the
+    // bin of its first column, src - (16 k - delta); a 16-byte aligned
+    // source needs src - 16 k + delta - 15 even
+    for (int l = 0; l < L; ++l) out->ring_delta[l] = (int32_t)((out->srcL[l] + 1) & 1);
+    out->ring_R = out->ring_D = 0;
+    const int RD[2][2] = {{64, 2}, {128, 3}};
+    for (const auto &rd : RD)
+        if (rd[0] < pl.P && ring_fits(pl, *out, rd[0], rd[1])) {
+            out->ring_R = rd[0];
+            out->ring_D = rd[1];
+            break;
+        }
+    // chunk events per step (see Schedule::ringev)
+    out->ringev.assign((size_t)out->T, 0u);
+    std::vector<int> x(L, 0);
+    for (int t = 0; t < out->T; ++t) {
+        const uint32_t w = out->steps[(size_t)t];
+        uint32_t ev = 0;
+        for (int l = 0; l < L; ++l) {
+            if (!(w >> (2 * l) & 1u)) continue;
+            const int u = x[l] + out->ring_delta[l];
+            if (u > 0 && u % kRingChunk == 0) ev |= 1u << l;
+            if (x[l] % kRingChunk == kRingChunk - 1) ev |= 1u << (8 + l);
+            ++x[l];
+        }
+        out->ringev[(size_t)t] = ev;
+    }
+    out->dev.clear();
+    return 0;
+}
+
+Schedule *get_ring_schedule(Plan &pl, uint32_t mask, int *err)
+{
+    std::lock_guard<std::mutex> g(pl.mu);
+    auto it = pl.ring_schedules.find(mask);
+    if (it != pl.ring_schedules.end()) return it->second.get();
+    std::unique_ptr<Schedule> sc(new (std::nothrow) Schedule());
+    if (!sc) {
+        *err = -ENOMEM;
+        return nullptr;
+    }
+    const int r = build_ring_schedule(pl, mask, sc.get());
+    if (r) {
+        *err = r;
+        return nullptr;
+    }
+    Schedule *raw = sc.get();
+    pl.ring_schedules[mask] = std::move(sc);
+    return raw;
+}
+
 Schedule *get_schedule(Plan &pl, uint32_t mask, int *err)
 {
     std::lock_guard<std::mutex> g(pl.mu);
@@ -608,20 +779,31 @@ int schedule_on_device(Plan &pl, Schedule &sc, uint32_t **dev)
         *dev = it->second;
         return 0;
     }
-    // device copy: the step words, then the forward words
+    // device copy: the step words, then the forward words; a one-sided
+    // path also (step, forward, chunk event, 0) per step from the next
+    // multiple of 4 words, plus one zero entry
     uint32_t *d = nullptr;
     const size_t n = sc.steps.size();
-    const size_t bytes = std::max<size_t>(4, 2 * n * sizeof(uint32_t));
+    const size_t n4 = sc.one_sided ? (2 * n + 3) / 4 * 4 + 4 * (n + 1) : 2 * n;
+    const size_t bytes = std::max<size_t>(4, n4 * sizeof(uint32_t));
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e == cudaErrorMemoryAllocation) {
         record_cuda(e);
         return -ENOMEM;
     }
     if ((r = record_cuda(e))) return r;
-    std::vector<uint32_t> both(2 * n);
+    std::vector<uint32_t> both(n4, 0u);
     std::copy(sc.steps.begin(), sc.steps.end(), both.begin());
     std::copy(sc.fwdw.begin(), sc.fwdw.end(), both.begin() + n);
-    if (n && (r = record_cuda(cudaMemcpy(d, both.data(), 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice)))) {
+    if (sc.one_sided) {
+        const size_t b4 = (2 * n + 3) / 4 * 4;
+        for (size_t t = 0; t < n; ++t) {
+            both[b4 + 4 * t] = sc.steps[t];
+            both[b4 + 4 * t + 1] = sc.fwdw[t];
+            both[b4 + 4 * t + 2] = t < sc.ringev.size() ? sc.ringev[t] : 0u;
+        }
+    }
+    if (n && (r = record_cuda(cudaMemcpy(d, both.data(), n4 * sizeof(uint32_t), cudaMemcpyHostToDevice)))) {
         cudaFree(d);
         return r;
     }

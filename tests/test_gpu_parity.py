@@ -211,7 +211,7 @@ def test_full_size_wide_geometry():
     _full_size(128, 8, TWELVE, 262144, ms[7::83])
 
 
-VARIANTS = [("ilv", {}), ("ilv", {"MOJETTE_DECODE_G": "5"}), ("ilv", {"MOJETTE_DECODE_G": "16"}),
+VARIANTS = [("ring", {}), ("ilv", {}), ("ilv", {"MOJETTE_DECODE_G": "5"}), ("ilv", {"MOJETTE_DECODE_G": "16"}),
             ("lines", {}), ("lines", {"MOJETTE_DECODE_ROWOFF": "0"}), ("fronts", {}), ("stream", {}),
             ("cols", {}), ("vander", {}), ("vander", {"MOJETTE_DECODE_GPC": "1"})]
 
@@ -244,7 +244,7 @@ def test_every_decode_kernel_variant(monkeypatch, kernel, K, name, P, Q, p):
         assert (host(out) == img).all(), (kernel, K, name, m)
 
 
-@pytest.mark.parametrize("kernel", ["ilv", "lines"])
+@pytest.mark.parametrize("kernel", ["ring", "ilv", "lines"])
 def test_path_kernels_8k_6x4_large_launch(monkeypatch, kernel):
     """The Sec. 2.2 path kernels at the headline geometry, 8 KB (6,4) (P = 256,
     Q = 4), in a launch of 4096 + 77 stripes -- large enough for decode_lines'
@@ -264,6 +264,34 @@ def test_path_kernels_8k_6x4_large_launch(monkeypatch, kernel):
         out.fill_(0x5A)
         mj.mojette_decode(plan, d_proj, m, out, S)
         assert (host(out) == ref).all(), (kernel, m)
+
+
+RING_GEOMS = [("4KB(6,4)", 128, 4, SIX), ("8KB(6,4)", 256, 4, SIX), ("16KB(6,4)", 512, 4, SIX),
+              ("4KB(3,2)", 256, 2, [-1, 1, 2]), ("8KB(3,2)", 512, 2, [-1, 1, 2]),
+              ("odd directions", 96, 3, [-5, -2, 1, 4, 7])]
+
+
+@pytest.mark.parametrize("name,P,Q,p", RING_GEOMS)
+@pytest.mark.parametrize("S", [1, 13, 2053])
+def test_ring_decode_every_mask(monkeypatch, name, P, Q, p, S):
+    """decode_ring (the one-sided path, each stripe's lines held as rings of
+    64 or 128 words fed by 128-byte bulk copies): every k-of-n and every
+    smaller erasure mask, ragged work items, against the oracle; the kernel
+    really runs (the path fits a ring at these geometries)."""
+    monkeypatch.setenv("MOJETTE_DECODE_KERNEL", "ring")
+    n = len(p)
+    img = inputs.stripes(S, Q, P, seed=13 * P + Q + S)
+    proj = oracle.encode(img, p, threads=8)
+    plan = mj.mojette_plan(P, Q, p)
+    d_proj = dev(proj)
+    out = empty((S, Q, P))
+    masks = [m for m in range(1 << n) if n - bin(m).count("1") >= Q]
+    masks = masks if S < 1000 else masks[:: max(1, len(masks) // 6)]
+    for m in masks:
+        assert mj.mojette_decode_kernel(plan, m, S) == "decode_ring", (name, m)
+        out.fill_(0x66)
+        mj.mojette_decode(plan, d_proj, m, out, S)
+        assert (host(out) == img).all(), (name, m)
 
 
 def test_stage_survivors_then_decode():
@@ -432,7 +460,7 @@ TWO_LINE = [("4KB(3,2)", 256, 2, [-1, 1, 2]), ("8KB(3,2)", 512, 2, [-1, 1, 2]),
             ("one pixel", 1, 2, [-1, 2]), ("odd", 37, 2, [0, 5])]
 
 
-@pytest.mark.parametrize("kernel", ["default", "scan", "lines"])
+@pytest.mark.parametrize("kernel", ["default", "scan", "lines", "ring"])
 @pytest.mark.parametrize("name,P,Q,p", TWO_LINE)
 @pytest.mark.parametrize("S", [1, 5, 4096 + 7])
 def test_two_line_closed_form(monkeypatch, kernel, name, P, Q, p, S):
