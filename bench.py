@@ -74,6 +74,9 @@ WORKLOADS = {
     "profile_wide8k": dict(P=128, Q=8, p=TWELVE, S=32768, erasures=4, mask_sample=1,
                            desc="32768 stripes x 8 KB (Q=8, P=128), (12,8); encode + 1 four-erasure decode "
                                 "(small case for ncu captures; 268 MB image > L2)"),
+    "profile_wide4k": dict(P=64, Q=8, p=TWELVE, S=65536, erasures=4, mask_sample=1,
+                           desc="65536 stripes x 4 KB (Q=8, P=64), (12,8); encode + 1 four-erasure decode "
+                                "(small case for ncu captures; 268 MB image > L2)"),
     "plain": dict(P=128, Q=4, p=SIX, S=1024, erasures=2,
                   desc="1024 stripes x 4 KB (Q=4, P=128), (6,4); encode + 15 two-erasure decodes"),
     "wide_4k": dict(P=64, Q=8, p=TWELVE, S=262144, erasures=4, mask_sample=15,

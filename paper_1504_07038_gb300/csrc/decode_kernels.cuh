@@ -42,6 +42,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "ptx.cuh"
 
@@ -414,13 +415,36 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
     int dk[Q > 1 ? Q - 1 : 1];
     uint32_t rk[Q > 1 ? Q - 1 : 1];
     uint32_t sfw = 0u;
-    uint32_t slink[4] = {0u, 0u, 0u, 0u};
-    int chain = 0;   // steady steps: lines l+1 .. l+chain are linked to this one
+    // steady steps, as all-ones / zero masks: Q <= 4, lm[d - 1] -- line
+    // l + d is linked to this one (lines l+1 .. l+d all linked); Q > 4,
+    // lm[r] -- this line is still linked after scan round r
+    uint32_t lm[Q > 1 ? Q - 1 : 1];
+    int smc = 0;
     auto load_group = [&](const DecGroup &gr) {
         const int T = gr.T;
         T4 = (T + 3) & ~3;
-        for (int t = lane; t < T4; t += 32)
-            stw[t] = t < T ? make_uint2(gr.steps[t], gr.steps[T + t]) : make_uint2(0u, 0u);
+        // the table in shared memory: step word; forward word's links (bits
+        // 0 .. 2Q-1) with the step's longest same-step chain (links l -> l+1
+        // -> ... in a row, either side) in bits 24..27, so that a step runs
+        // only the shuffle rounds some chain needs
+        for (int t = lane; t < T4; t += 32) {
+            uint32_t w = 0u, f = 0u;
+            if (t < T) {
+                w = gr.steps[t];
+                f = gr.steps[T + t] & ((1u << (2 * Q)) - 1u);
+            }
+            uint32_t mc = 0u;
+#pragma unroll
+            for (int sd = 0; sd < 2; ++sd) {
+                uint32_t run = 0u;
+#pragma unroll
+                for (int j = 0; j + 1 < Q; ++j) {
+                    run = ((f >> (2 * j + sd)) & 1u) ? run + 1u : 0u;
+                    mc = max(mc, run);
+                }
+            }
+            stw[t] = make_uint2(w, f | (mc << 24));
+        }
         const int p = gr.p[ls];
         const uint32_t ord = gr.order[ls];   // nibble 0 is the own bin
 #pragma unroll
@@ -430,20 +454,31 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             rk[k - 1] = wbase + (uint32_t)(g * a.SWr + a.rowbase[l2] + (REV ? P - 1 : 0)) * 8u;
         }
         sfw = ok ? (gr.fwd >> ls) & 1u : 0u;
-        chain = 0;
-        if (ok)
-            for (int j = l; j + 1 < Q && ((gr.fwd >> (2 * j + side)) & 1u); ++j) ++chain;
-        uint32_t c[Q];
+        smc = 0;   // the steady pattern's longest chain (the same in every lane)
+        for (int sd = 0; sd < 2; ++sd)
+            for (int j = 0, run = 0; j + 1 < Q; ++j) {
+                run = ((gr.fwd >> (2 * j + sd)) & 1u) ? run + 1 : 0;
+                smc = max(smc, run);
+            }
+        if constexpr (Q <= 4) {
+            int chain = 0;   // lines l+1 .. l+chain are linked to this one
+            if (ok)
+                for (int j = l; j + 1 < Q && ((gr.fwd >> (2 * j + side)) & 1u); ++j) ++chain;
 #pragma unroll
-        for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
+            for (int d = 1; d < Q; ++d) lm[d - 1] = d <= chain ? ~0u : 0u;
+        } else {
+            uint32_t c[Q];
 #pragma unroll
-        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
-            slink[r] = ok ? c[l] : 0u;
-            uint32_t nc[Q];
+            for (int j = 0; j < Q; ++j) c[j] = (j + 1 < Q) ? (gr.fwd >> (2 * j + side)) & 1u : 0u;
 #pragma unroll
-            for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+            for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                lm[r] = ok && c[l] ? ~0u : 0u;
+                uint32_t nc[Q];
 #pragma unroll
-            for (int j = 0; j < Q; ++j) c[j] = nc[j];
+                for (int j = 0; j < Q; ++j) nc[j] = (c[j] && j + d < Q) ? c[j + d] : 0u;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) c[j] = nc[j];
+            }
         }
     };
     const DecGroup *gp = nullptr;   // batched: the current work item's path
@@ -580,87 +615,124 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         // the next step's words are read one step ahead, as one 64-bit word
         // (the table holds T4 + 4 pairs, so the read past the last step
         // stays inside it)
-        uint2 nx = stw[0];
-        for (int t = 0; t < T4; ++t) {
-            const uint32_t w = nx.x, f = nx.y;
-            nx = stw[t + 1];
-            if (w & kStepSteady) {
-                // steady: every line moves, links are the path's pattern
-                const uint64_t own = ld_s64(pos);
-                uint64_t lv[Q > 1 ? Q - 1 : 1];
-#pragma unroll
-                for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
-                const uint32_t at = pos;
-                pos += stepb;
-                x += dx;
-                set_oa();
-                uint64_t v = 0;
-#pragma unroll
-                for (int k = 0; k < Q - 1; ++k) v ^= lv[k];
-                if constexpr (Q <= 4) {
-                    // the linked lines' own values, all fetched at once: one
-                    // shuffle latency instead of log2 Q dependent rounds
-                    const uint64_t x0 = v;
-#pragma unroll
-                    for (int d = 1; d < Q; ++d) {
-                        const uint64_t tv = __shfl_down_sync(0xffffffffu, x0, d * G);
-                        if (d <= chain) v ^= tv;
+        // The step loop, compiled once per bound MC on the steady pattern's
+        // longest same-step chain (steady steps run only the shuffle rounds
+        // d <= MC; a bound known at compile time costs no branch); other
+        // steps skip the rounds their own longest chain does not need.
+        auto run_steps = [&](auto mcc) {
+            constexpr int MC = decltype(mcc)::value;
+            uint2 nx = stw[0];
+            for (int t = 0; t < T4; ++t) {
+                const uint32_t w = nx.x, f = nx.y;
+                const int mc = (int)(f >> 24);   // longest same-step chain
+                nx = stw[t + 1];
+                if (w & kStepSteady) {
+                    // steady: every line moves, links are the path's pattern
+                    const uint64_t own = ld_s64(pos);
+                    uint64_t lv[Q > 1 ? Q - 1 : 1];
+    #pragma unroll
+                    for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
+                    const uint32_t at = pos;
+                    pos += stepb;
+                    x += dx;
+                    set_oa();
+                    // in 32-bit halves: a masked XOR is one 3-input logic op
+                    uint32_t xl = 0u, xh = 0u;
+    #pragma unroll
+                    for (int k = 0; k < Q - 1; ++k) {
+                        xl ^= (uint32_t)lv[k];
+                        xh ^= (uint32_t)(lv[k] >> 32);
                     }
-                } else {
-#pragma unroll
-                    for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                    uint32_t vl, vh;
+                    if constexpr (Q <= 4) {
+                        // the linked lines' own values, all fetched at once: one
+                        // shuffle latency instead of log2 Q dependent rounds
+                        vl = xl ^ (uint32_t)own;
+                        vh = xh ^ (uint32_t)(own >> 32);
+    #pragma unroll
+                        for (int d = 1; d < Q; ++d) {
+                            if (d <= MC) {   // a constant once unrolled
+                                vl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[d - 1];
+                                vh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[d - 1];
+                            }
+                        }
+                    } else {
+    #pragma unroll
+                        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                            if (d <= MC) {
+                                xl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[r];
+                                xh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[r];
+                            }
+                        }
+                        vl = xl ^ (uint32_t)own;
+                        vh = xh ^ (uint32_t)(own >> 32);
+                    }
+                    st_s64_if(at, ((uint64_t)vh << 32) | vl, ok);
+                    __syncwarp();
+                    continue;
+                }
+                // a front that does not move this step loads nothing (its value
+                // is not used: a link always points at a front that moves)
+                const uint32_t act = w & bitmask;
+                const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
+                uint64_t own = 0, v = 0;
+                if (act) {
+                    own = ld_s64(pos);
+    #pragma unroll
+                    for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(addr(k));
+                }
+                // segmented suffix XOR: v_l ^= v_{l+1} while linked (only the
+                // rounds the step's longest chain needs)
+                uint32_t c = fw;
+    #pragma unroll
+                for (int d = 1; d < Q; d <<= 1) {
+                    if (d <= mc) {
                         const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
-                        if (slink[r]) v ^= tv;
+                        const uint32_t tc = __shfl_down_sync(0xffffffffu, c, d * G);
+                        if (c) {
+                            v ^= tv;
+                            c = tc;
+                        }
                     }
                 }
-                st_s64_if(at, v ^ own, ok);
+                st_s64_if(pos, v ^ own, act);
+                pos += act ? stepb : 0;
+                x += act ? dx : 0;
+                set_oa();
                 __syncwarp();
-                continue;
             }
-            // a front that does not move this step loads nothing (its value
-            // is not used: a link always points at a front that moves)
-            const uint32_t act = w & bitmask;
-            const uint32_t fw = ok ? (f >> ls) & 1u : 0u;
-            uint64_t own = 0, v = 0;
-            if (act) {
-                own = ld_s64(pos);
-#pragma unroll
-                for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(addr(k));
+        };
+        if constexpr (Q <= 4) {
+            switch (smc) {
+            case 0: run_steps(std::integral_constant<int, 0>{}); break;
+            case 1: run_steps(std::integral_constant<int, 1>{}); break;
+            case 2: run_steps(std::integral_constant<int, 2>{}); break;
+            default: run_steps(std::integral_constant<int, 3>{}); break;
             }
-            // segmented suffix XOR: v_l ^= v_{l+1} while linked
-            uint32_t c = fw;
-#pragma unroll
-            for (int d = 1; d < Q; d <<= 1) {
-                const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
-                const uint32_t tc = __shfl_down_sync(0xffffffffu, c, d * G);
-                if (c) {
-                    v ^= tv;
-                    c = tc;
-                }
-            }
-            st_s64_if(pos, v ^ own, act);
-            pos += act ? stepb : 0;
-            x += act ? dx : 0;
-            set_oa();
-            __syncwarp();
+        } else {
+            // scan rounds of stride 1, 2, 4: a chain of length c needs those <= c
+            if (smc == 0) run_steps(std::integral_constant<int, 0>{});
+            else if (smc == 1) run_steps(std::integral_constant<int, 1>{});
+            else if (smc <= 3) run_steps(std::integral_constant<int, 3>{});
+            else run_steps(std::integral_constant<int, 7>{});
         }
 
         // write-back, coalesced along each row: the image's lines (the lost
-        // data lines, in place, for the systematic form)
+        // data lines, in place, for the systematic form). The loop is
+        // unrolled so that several shared loads are in flight at once (one
+        // at a time, the write-back took about a quarter of an item's time
+        // at 8 KB (6,4)); 16-byte stores of word pairs measured slower (a
+        // half-warp's loads then span twice the banks).
         if (copy_ok && gg < nst) {
-            if constexpr (SYS) {
-                uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)a.Qd * P;
-                for (int ll = 0; ll < Q; ++ll) {
-                    const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll];
-                    uint64_t *o = out + (int64_t)grp().lpos[ll] * P;
-                    for (int xx = xk; xx < P; xx += XK) __stcs(o + xx, row[xx]);
-                }
-            } else {
-                uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)Q * P;
-                for (int ll = 0; ll < Q; ++ll) {
-                    const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll] + (P - 1);
-                    for (int xx = xk; xx < P; xx += XK) __stcs(out + ll * P + xx, row[-xx]);
-                }
+            uint64_t *out = BATCHED ? a.dstp[first + gg] : a.img + (s0 + gg) * (int64_t)(SYS ? a.Qd : Q) * P;
+            for (int ll = 0; ll < Q; ++ll) {
+                // column x of the row at row[dir * x]: pixel order (systematic)
+                // or bin order from its last word
+                const uint64_t *row = wbuf + gg * a.SWr + a.rowbase[ll] + (SYS ? 0 : P - 1);
+                constexpr int dir = SYS ? 1 : -1;
+                uint64_t *o = out + (int64_t)(SYS ? grp().lpos[ll] : ll) * P;
+#pragma unroll 4
+                for (int xx = xk; xx < P; xx += XK) __stcs(o + xx, row[dir * xx]);
             }
         }
         __syncwarp();
