@@ -52,7 +52,7 @@ namespace {
 // pos[1] < ... (all rows 0 .. Q-1 otherwise); the other pixel of a bin line
 // on line l2 is then (l2, x + (pos[l2] - pos[l]) p).
 int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines, int limit,
-          Schedule *out, bool one_sided = false)
+          Schedule *out, bool one_sided = false, int maxchain = kMaxLines)
 {
     const int P = pl.P, Q = lines;
     const int sides = one_sided ? 1 : 2;
@@ -66,7 +66,9 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
     std::vector<uint8_t> who((size_t)P * Q, 0);
     std::vector<int32_t> when((size_t)P * Q, 0);
     int last_sync = 0;   // a synchronisation before the loads of this step
-    int a[kMaxLines], z[kMaxLines], took[2][kMaxLines];
+    // chain[side][l]: how many lines l+1, l+2, ... line l's front reaches
+    // through same-step values in the current step (at most `maxchain`)
+    int a[kMaxLines], z[kMaxLines], took[2][kMaxLines], chain[2][kMaxLines];
     for (int l = 0; l < Q; ++l) { a[l] = 0; z[l] = P - 1; }
     int64_t remaining = (int64_t)P * Q;
     std::vector<uint32_t> steps, pattern;
@@ -79,21 +81,26 @@ int sweep(const Plan &pl, const std::vector<int> &asc, const int *pos, int lines
         for (int side = 0; side < sides; ++side) {
             for (int l = Q - 1; l >= 0; --l) {
                 took[side][l] = -1;
+                chain[side][l] = 0;
                 if (a[l] > z[l]) continue;
                 const int x = side ? z[l] : a[l];
                 if (side == 1 && took[0][l] == x) continue;   // the fronts met on this pixel
                 const int p = pF[side][l];
-                bool ready = true;
+                bool ready = true, linked = false;
                 for (int l2 = 0; l2 < Q && ready; ++l2) {
                     if (l2 == l) continue;
                     const int64_t x2 = (int64_t)x + (int64_t)(pos[l2] - pos[l]) * p;
                     if (x2 < 0 || x2 >= P) continue;
                     if (known[(size_t)l2 * P + x2]) continue;
-                    if (l2 == l + 1 && took[side][l2] == x2) continue;
+                    if (l2 == l + 1 && took[side][l2] == x2 && chain[side][l2] < maxchain) {
+                        linked = true;
+                        continue;
+                    }
                     ready = false;
                 }
                 if (ready) {
                     took[side][l] = x;
+                    chain[side][l] = linked ? chain[side][l + 1] + 1 : 0;
                     word |= 1u << (2 * l + side);
                 }
             }
@@ -502,10 +509,24 @@ int build_schedule(const Plan &pl, uint32_t mask, Schedule *out)
             break;
         }
         const int limit = best < 0 ? (1 << 30) : best;
-        const int T = sweep(pl, asc, pos, L, limit, &tmp);
+        int T = sweep(pl, asc, pos, L, limit, &tmp);
         if (T >= 0 && (best < 0 || T < best)) {
             best = T;
             *out = tmp;
+            // The same path length with shorter same-step chains, where one
+            // exists: decode_lines runs a shuffle round per chain link it may
+            // meet in a steady step (Q <= 4: one per link of the longest
+            // chain; Q > 4: rounds of stride 1, 2, 4), so prefer bound 1,
+            // then 2 (Q <= 4) or 3 (Q > 4), never at the cost of a step.
+            const int bounds[2] = {1, L <= 4 ? 2 : 3};
+            for (int b : bounds) {
+                if (b >= L - 1) break;
+                Schedule alt;
+                if (sweep(pl, asc, pos, L, best + 1, &alt, false, b) == best) {
+                    *out = alt;
+                    break;
+                }
+            }
         }
         if (++tried >= kMaxCandidates) break;
         // next combination of L out of m
