@@ -525,9 +525,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
         // rebuilds); systematic: the lanes of the left side each a whole
         // residual row. Where the run and its place in shared memory agree
         // mod 16 bytes, one bulk copy takes the aligned middle and 8-byte
-        // cp.async the odd word at either end; the other runs are copied by
-        // the whole warp, word by word. The previous item's reads and
-        // writes of the regions are ordered before the bulk writes first.
+        // cp.async the odd word at either end. Where they do not, the run's
+        // first n - 1 words are staged the same way one word further on
+        // (which makes them agree), its last word is loaded into a
+        // register, and once the copies have landed the warp moves the run
+        // down one word and puts the last word in place. The previous item's
+        // reads and writes of the regions are ordered before the bulk
+        // writes first.
         fence_proxy_async_smem();
         __syncwarp();
         int n = 0;
@@ -555,25 +559,16 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 }
             }
         }
-        const bool same = n > 0 && ((((uint32_t)(uintptr_t)gsrc) ^ sdst) & 8u) == 0;
-        const int head = same && ((uintptr_t)gsrc & 8u) ? 1 : 0;
-        const int body = same ? ((n - head) & ~1) : 0;
+        const bool shifted = n > 0 && ((((uint32_t)(uintptr_t)gsrc) ^ sdst) & 8u) != 0;
+        const int n1 = shifted ? n - 1 : n;                    // words staged by copies
+        const uint32_t sd1 = shifted ? sdst + 8u : sdst;        // where they land
+        const int head = n1 > 0 && ((uintptr_t)gsrc & 8u) ? 1 : 0;
+        const int body = n1 > 0 ? ((n1 - head) & ~1) : 0;
         mbar_arrive_expect_tx(bar, (uint32_t)body * 8u);
-        if (body > 0) tma_load_1d(sdst + head * 8u, gsrc + head, (uint32_t)body * 8u, bar);
-        if (same) {
-            if (head) cp_async8_s(sdst, gsrc);
-            if (n - head - body) cp_async8_s(sdst + (uint32_t)(n - 1) * 8u, gsrc + (n - 1));
-        }
-        uint32_t rest = __ballot_sync(0xffffffffu, n > 0 && !same);
-        while (rest) {
-            const int src_lane = __ffs(rest) - 1;
-            rest &= rest - 1;
-            const int nn = __shfl_sync(0xffffffffu, n, src_lane);
-            const uint64_t *gs = reinterpret_cast<const uint64_t *>(
-                __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)gsrc, src_lane));
-            const uint32_t sd = __shfl_sync(0xffffffffu, sdst, src_lane);
-            for (int i = lane; i < nn; i += 32) cp_async8_s(sd + (uint32_t)i * 8u, gs + i);
-        }
+        if (body > 0) tma_load_1d(sd1 + head * 8u, gsrc + head, (uint32_t)body * 8u, bar);
+        if (head) cp_async8_s(sd1, gsrc);
+        if (n1 - head - body > 0) cp_async8_s(sd1 + (uint32_t)(n1 - 1) * 8u, gsrc + (n1 - 1));
+        const uint64_t lastw = shifted ? gsrc[n - 1] : 0ull;
         cp_async_wait_all();
         const bool arrived = mbar_wait_bounded(bar, phase);
         phase ^= 1u;
@@ -586,6 +581,38 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             return;
         }
         __syncwarp();
+        // the shifted runs, one at a time by the whole warp: every word read
+        // before any is written
+        uint32_t rest = __ballot_sync(0xffffffffu, shifted);
+        while (rest) {
+            const int src_lane = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int nn = __shfl_sync(0xffffffffu, n, src_lane);
+            const uint32_t sd = __shfl_sync(0xffffffffu, sdst, src_lane);
+            const uint64_t lw = __shfl_sync(0xffffffffu, (unsigned long long)lastw, src_lane);
+            // K words per lane per round (K * 32 >= the run where it fits)
+            auto shift_down = [&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+                for (int i0 = 0; i0 < nn; i0 += 32 * K) {
+                    uint64_t w[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int i = i0 + k * 32 + lane;
+                        w[k] = i + 1 < nn ? ld_s64(sd + (uint32_t)(i + 1) * 8u) : lw;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int i = i0 + k * 32 + lane;
+                        if (i < nn) st_s64(sd + (uint32_t)i * 8u, w[k]);
+                    }
+                    __syncwarp();
+                }
+            };
+            if (nn > 64) shift_down(std::integral_constant<int, 4>{});
+            else if (nn > 32) shift_down(std::integral_constant<int, 2>{});
+            else shift_down(std::integral_constant<int, 1>{});
+        }
 
         uint32_t pos = start;
         int x = side ? P - 1 : 0;          // this front's column
