@@ -445,6 +445,27 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             }
             stw[t] = make_uint2(w, f | (mc << 24));
         }
+        // bits 16..30 of a steady step's word: the steady steps from it on,
+        // 32 entries at a time from the end (the next non-steady entry by
+        // ballot; the count carried in from the chunk after)
+        __syncwarp();
+        uint32_t carry = 0u;
+        for (int base = ((T4 - 1) / 32) * 32; base >= 0; base -= 32) {
+            const int t = base + lane;
+            const bool in = t < T4;
+            uint2 e = in ? stw[t] : make_uint2(0u, 0u);
+            const bool st = in && (e.x & kStepSteady);
+            const uint32_t above = __ballot_sync(0xffffffffu, !st) & ~((2u << lane) - 1u);
+            uint32_t run = 0u;
+            if (st) run = above ? (uint32_t)(__ffs(above) - 1 - lane) : 32u - lane + carry;
+            run = min(run, 0x7fffu);
+            if (in) {
+                e.x = (e.x & ~(0x7fffu << 16)) | (run << 16);
+                stw[t] = e;
+            }
+            carry = __shfl_sync(0xffffffffu, run, 0);
+        }
+        __syncwarp();
         const int p = gr.p[ls];
         const uint32_t ord = gr.order[ls];   // nibble 0 is the own bin
 #pragma unroll
@@ -655,47 +676,61 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 nx = stw[t + 1];
                 if (w & kStepSteady) {
                     // steady: every line moves, links are the path's pattern
-                    const uint64_t own = ld_s64(pos);
-                    uint64_t lv[Q > 1 ? Q - 1 : 1];
-    #pragma unroll
-                    for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
-                    const uint32_t at = pos;
-                    pos += stepb;
-                    x += dx;
-                    set_oa();
-                    // in 32-bit halves: a masked XOR is one 3-input logic op
-                    uint32_t xl = 0u, xh = 0u;
-    #pragma unroll
-                    for (int k = 0; k < Q - 1; ++k) {
-                        xl ^= (uint32_t)lv[k];
-                        xh ^= (uint32_t)(lv[k] >> 32);
-                    }
-                    uint32_t vl, vh;
+                    auto steady_step = [&]() {
+                        const uint64_t own = ld_s64(pos);
+                        uint64_t lv[Q > 1 ? Q - 1 : 1];
+#pragma unroll
+                        for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
+                        const uint32_t at = pos;
+                        pos += stepb;
+                        x += dx;
+                        set_oa();
+                        // in 32-bit halves: a masked XOR is one 3-input logic op
+                        uint32_t xl = 0u, xh = 0u;
+#pragma unroll
+                        for (int k = 0; k < Q - 1; ++k) {
+                            xl ^= (uint32_t)lv[k];
+                            xh ^= (uint32_t)(lv[k] >> 32);
+                        }
+                        uint32_t vl, vh;
+                        if constexpr (Q <= 4) {
+                            // the linked lines' own values, all fetched at once: one
+                            // shuffle latency instead of log2 Q dependent rounds
+                            vl = xl ^ (uint32_t)own;
+                            vh = xh ^ (uint32_t)(own >> 32);
+#pragma unroll
+                            for (int d = 1; d < Q; ++d) {
+                                if (d <= MC) {   // a constant once unrolled
+                                    vl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[d - 1];
+                                    vh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[d - 1];
+                                }
+                            }
+                        } else {
+#pragma unroll
+                            for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
+                                if (d <= MC) {
+                                    xl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[r];
+                                    xh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[r];
+                                }
+                            }
+                            vl = xl ^ (uint32_t)own;
+                            vh = xh ^ (uint32_t)(own >> 32);
+                        }
+                        st_s64_if(at, ((uint64_t)vh << 32) | vl, ok);
+                        __syncwarp();
+                    };
                     if constexpr (Q <= 4) {
-                        // the linked lines' own values, all fetched at once: one
-                        // shuffle latency instead of log2 Q dependent rounds
-                        vl = xl ^ (uint32_t)own;
-                        vh = xh ^ (uint32_t)(own >> 32);
-    #pragma unroll
-                        for (int d = 1; d < Q; ++d) {
-                            if (d <= MC) {   // a constant once unrolled
-                                vl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[d - 1];
-                                vh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[d - 1];
-                            }
-                        }
+                        // a run of steady steps (its length in bits 16..30 of
+                        // the step word), the table not read until it ends
+                        // (at Q > 4 one step at a time measured faster)
+                        const int run = (int)((w >> 16) & 0x7fffu);
+#pragma unroll 2
+                        for (int rs = 0; rs < run; ++rs) steady_step();
+                        t += run - 1;
+                        nx = stw[t + 1];
                     } else {
-    #pragma unroll
-                        for (int r = 0, d = 1; d < Q; ++r, d <<= 1) {
-                            if (d <= MC) {
-                                xl ^= __shfl_down_sync(0xffffffffu, xl, d * G) & lm[r];
-                                xh ^= __shfl_down_sync(0xffffffffu, xh, d * G) & lm[r];
-                            }
-                        }
-                        vl = xl ^ (uint32_t)own;
-                        vh = xh ^ (uint32_t)(own >> 32);
+                        steady_step();
                     }
-                    st_s64_if(at, ((uint64_t)vh << 32) | vl, ok);
-                    __syncwarp();
                     continue;
                 }
                 // a front that does not move this step loads nothing (its value
@@ -705,13 +740,13 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 uint64_t own = 0, v = 0;
                 if (act) {
                     own = ld_s64(pos);
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(addr(k));
                 }
                 // segmented suffix XOR: v_l ^= v_{l+1} while linked (only the
                 // rounds the step's longest chain needs)
                 uint32_t c = fw;
-    #pragma unroll
+#pragma unroll
                 for (int d = 1; d < Q; d <<= 1) {
                     if (d <= mc) {
                         const uint64_t tv = __shfl_down_sync(0xffffffffu, v, d * G);
