@@ -660,15 +660,15 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             else return opaddr(k);
         };
         set_oa();
-        // the next step's words are read one step ahead, as one 64-bit word
-        // (the table holds T4 + 4 pairs, so the read past the last step
-        // stays inside it)
         // The step loop, compiled once per bound MC on the steady pattern's
         // longest same-step chain (steady steps run only the shuffle rounds
         // d <= MC; a bound known at compile time costs no branch); other
         // steps skip the rounds their own longest chain does not need.
         auto run_steps = [&](auto mcc) {
             constexpr int MC = decltype(mcc)::value;
+            // the next step's words are read one step ahead, as one 64-bit
+            // word (the table holds T4 + 4 pairs, so the read past the last
+            // step stays inside it)
             uint2 nx = stw[0];
             for (int t = 0; t < T4; ++t) {
                 const uint32_t w = nx.x, f = nx.y;
@@ -676,15 +676,24 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 nx = stw[t + 1];
                 if (w & kStepSteady) {
                     // steady: every line moves, links are the path's pattern
-                    auto steady_step = [&]() {
+                    // FAST: every operand of every lane lies inside the
+                    // image for the whole step, so the addresses just move
+                    // with the front (no clamp); x is caught up afterwards
+                    auto steady_step = [&](auto fastc) {
+                        constexpr bool FAST = decltype(fastc)::value;
                         const uint64_t own = ld_s64(pos);
                         uint64_t lv[Q > 1 ? Q - 1 : 1];
 #pragma unroll
                         for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
                         const uint32_t at = pos;
                         pos += stepb;
-                        x += dx;
-                        set_oa();
+                        if constexpr (FAST) {
+#pragma unroll
+                            for (int k = 0; k < Q - 1; ++k) oa[k] += stepb;
+                        } else {
+                            x += dx;
+                            set_oa();
+                        }
                         // in 32-bit halves: a masked XOR is one 3-input logic op
                         uint32_t xl = 0u, xh = 0u;
 #pragma unroll
@@ -724,12 +733,33 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                         // the step word), the table not read until it ends
                         // (at Q > 4 one step at a time measured faster)
                         const int run = (int)((w >> 16) & 0x7fffu);
+                        // steps [s0, s1) of the run: every lane's operand
+                        // columns x + dk (moving by dx per step) inside [0, P)
+                        int lo = 0, hi = run;
+                        if (ok) {
+#pragma unroll
+                            for (int k = 0; k < Q - 1; ++k) {
+                                const int c = x + dk[k];
+                                if (dx > 0) {
+                                    lo = max(lo, -c);
+                                    hi = min(hi, P - c);
+                                } else {
+                                    lo = max(lo, c - (P - 1));
+                                    hi = min(hi, c + 1);
+                                }
+                            }
+                        }
+                        const int s0 = min(__reduce_max_sync(0xffffffffu, lo), run);
+                        const int s1 = max(__reduce_min_sync(0xffffffffu, hi), s0);
+                        for (int rs = 0; rs < s0; ++rs) steady_step(std::false_type{});
 #pragma unroll 2
-                        for (int rs = 0; rs < run; ++rs) steady_step();
+                        for (int rs = s0; rs < s1; ++rs) steady_step(std::true_type{});
+                        x += dx * (s1 - s0);
+                        for (int rs = s1; rs < run; ++rs) steady_step(std::false_type{});
                         t += run - 1;
                         nx = stw[t + 1];
                     } else {
-                        steady_step();
+                        steady_step(std::false_type{});
                     }
                     continue;
                 }
