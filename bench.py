@@ -491,50 +491,98 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
     image in and the projections out (encode), then for each mask the
     projections the decode reads in (mojette_stage_survivors: the Q
     surviving projections' slices, what a storage read fetches) and the
-    image out, from/to pinned host memory. The stripes are cut into `chunks`
-    slices that alternate over two streams, each slice's copies and kernels
-    in order on its stream, so one slice's host-to-device copy overlaps
-    another's device-to-host copy and kernels. Decode reads a separate
-    device buffer, filled with junk before the timed region, so the
-    round-trip check shows the copied data is what is used."""
+    image out, from/to pinned host memory. Three streams -- host-to-device
+    copies, kernels, device-to-host copies -- ordered by events, so that
+    both copy directions run back to back while the kernels run; the stripes
+    are cut into `chunks` slices, and the decode's input and output buffers
+    are doubled (mask k uses buffer k mod 2), so the copies of one mask
+    overlap the decode of the next. Decode reads a separate device buffer,
+    filled with junk before the timed region, so the round-trip check shows
+    the copied data is what is used."""
     import torch
     from paper_1504_07038_gb300 import binding as mj
 
     S, Q, P = w["S"], w["Q"], w["P"]
     h_proj = torch.empty((S, plan.total), dtype=torch.int64).pin_memory()
     h_out = torch.empty((S, Q, P), dtype=torch.int64).pin_memory()
-    d_in = torch.full((S, plan.total), 0x0BAD0BAD0BAD0BAD, dtype=torch.int64, device="cuda")
-    chunks, nstreams = args.e2e_chunks, args.e2e_streams
-    side = [torch.cuda.Stream() for _ in range(nstreams)]
+    d_in = [torch.full((S, plan.total), 0x0BAD0BAD0BAD0BAD, dtype=torch.int64, device="cuda")
+            for _ in range(2)]
+    d_o = [d_out, torch.empty_like(d_out)]
+    chunks = args.e2e_chunks
+    s_in, s_k, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     bounds = [(S * c // chunks, S * (c + 1) // chunks) for c in range(chunks)]
     staged = [0]
+    ev = lambda: torch.cuda.Event()   # noqa: E731
+    # per slice, the last event that used each buffer (carried across steps)
+    last = {key: [None] * chunks for key in ("enc", "proj", "stage_done", "dec0", "dec1", "out0", "out1")}
+
+    def after(st, e):
+        if e is not None:
+            st.wait_event(e)
 
     def step():
         staged[0] = 0
-        for st in side:
-            st.wait_stream(stream)
+        e_proj = [None] * chunks
         for c, (a, b) in enumerate(bounds):
-            st = side[c % nstreams]
-            with torch.cuda.stream(st):
+            after(s_in, last["enc"][c])                 # d_img slice free
+            with torch.cuda.stream(s_in):
                 d_img[a:b].copy_(h_img[a:b], non_blocking=True)
-                mj.mojette_encode(plan, d_img[a:b], d_proj[a:b], b - a, st)
+                e_img = ev(); e_img.record(s_in)
+            s_k.wait_event(e_img)
+            after(s_k, last["proj"][c])                 # d_proj slice copied out
+            with torch.cuda.stream(s_k):
+                mj.mojette_encode(plan, d_img[a:b], d_proj[a:b], b - a, s_k)
+                e_enc = ev(); e_enc.record(s_k)
+            last["enc"][c] = e_enc
+            s_out.wait_event(e_enc)
+            after(s_out, last["stage_done"][c])         # h_proj slice no longer read
+            with torch.cuda.stream(s_out):
                 h_proj[a:b].copy_(d_proj[a:b], non_blocking=True)
-                for m in masks:
-                    staged[0] += mj.mojette_stage_survivors(plan, h_proj[a:b], m, d_in[a:b], b - a, st)
-                    mj.mojette_decode(plan, d_in[a:b], m, d_out[a:b], b - a, st)
-                    h_out[a:b].copy_(d_out[a:b], non_blocking=True)
-        for st in side:
+                e = ev(); e.record(s_out)
+            e_proj[c] = e
+            last["proj"][c] = e
+        for k, m in enumerate(masks):
+            j = k % 2
+            for c, (a, b) in enumerate(bounds):
+                s_in.wait_event(e_proj[c])
+                after(s_in, last[f"dec{j}"][c])         # d_in[j] slice read by its last decode
+                with torch.cuda.stream(s_in):
+                    staged[0] += mj.mojette_stage_survivors(plan, h_proj[a:b], m, d_in[j][a:b], b - a, s_in)
+                    e_st = ev(); e_st.record(s_in)
+                last["stage_done"][c] = e_st
+                s_k.wait_event(e_st)
+                after(s_k, last[f"out{j}"][c])          # d_o[j] slice copied out
+                with torch.cuda.stream(s_k):
+                    mj.mojette_decode(plan, d_in[j][a:b], m, d_o[j][a:b], b - a, s_k)
+                    e_d = ev(); e_d.record(s_k)
+                last[f"dec{j}"][c] = e_d
+                s_out.wait_event(e_d)
+                with torch.cuda.stream(s_out):
+                    h_out[a:b].copy_(d_o[j][a:b], non_blocking=True)
+                    e_o = ev(); e_o.record(s_out)
+                last[f"out{j}"][c] = e_o
+
+    def fork():
+        for st in (s_in, s_k, s_out):
+            st.wait_stream(stream)
+
+    def join():
+        for st in (s_in, s_k, s_out):
             stream.wait_stream(st)
 
     steps = max(10, min(args.steps, 12))
+    fork()
     step()
+    join()
     torch.cuda.synchronize()
-    floor = copy_floor(h_proj, d_in)
+    floor = copy_floor(h_proj, d_in[0])
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(steps):
+    fork()
+    for _ in range(steps):   # steps overlap: each waits only on the buffers it reuses
         step()
+    join()
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
@@ -547,7 +595,9 @@ def run_e2e(args, w, plan, h_img, d_img, d_proj, d_out, masks, stream):
             "ms_per_step": round(ms, 3), "steps": steps, "round_trip_ok": ok,
             "copy_floor": {"ms": round(max(h2d / floor["h2d_gbs"], d2h / floor["d2h_gbs"],
                                            (h2d + d2h) / floor["both_gbs"]) / 1e6, 3), **floor},
-            "pipeline": f"{chunks} stripe slices over {nstreams} streams; decode inputs: surviving projections only",
+            "pipeline": (f"{chunks} stripe slices; host-to-device copies, kernels and device-to-host "
+                         "copies on three streams ordered by events; decode input and output "
+                         "double-buffered; decode inputs: surviving projections only"),
             "host": host_memory_note()}
 
 
@@ -920,7 +970,6 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=inputs.DEFAULT_SEED, help="seed of the stripe pixels")
     ap.add_argument("--e2e-chunks", type=int, default=8, help="stripe slices of the e2e pipeline")
-    ap.add_argument("--e2e-streams", type=int, default=2, help="streams of the e2e pipeline")
     ap.add_argument("--stripes", type=int, default=0, help="override the workload's stripe count")
     args = ap.parse_args()
     if args.warmup < 3:
