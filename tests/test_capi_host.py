@@ -466,6 +466,43 @@ def test_path_sync_marks_cover_every_cross_front_read():
                     x[side][l] += -1 if side else 1
 
 
+def _steady_chain(sc, Q):
+    """Longest run of same-step links (line l takes line l+1's value of the
+    same step) in the path's steady pattern, either side."""
+    steady = [t for t in range(sc["T"]) if sc["steps"][t] >> 31 & 1]
+    if not steady:
+        return 0
+    fwd = sc["forward"][steady[0]]
+    best = 0
+    for side in (0, 1):
+        run = 0
+        for j in range(Q - 1):
+            run = run + 1 if fwd >> (2 * j + side) & 1 else 0
+            best = max(best, run)
+    return best
+
+
+def test_paths_prefer_short_same_step_chains():
+    """Among the paths with the fewest steps the host keeps one whose
+    same-step chains are short: decode_lines runs one shuffle round per
+    link of a steady step's longest chain (Q <= 4) or per doubling round
+    (Q > 4). At 8 KB (6,4) every two-erasure path links at most two lines in
+    a row (three did on six masks before) and still takes at most 132 steps;
+    at 8 KB (12,8) most four-erasure paths need at most two scan rounds
+    (chains of at most 3 links)."""
+    six = [-3, -2, -1, 1, 2, 3]
+    plan = mj.mojette_plan(256, 4, six)
+    for m in inputs.all_masks(6, 2):
+        sc = mj.mojette_schedule(plan, m)
+        assert _steady_chain(sc, 4) <= 2, m
+        assert sc["T"] <= 132, (m, sc["T"])
+    twelve = [v for v in range(-6, 7) if v]
+    plan = mj.mojette_plan(128, 8, twelve)
+    masks = inputs.all_masks(12, 4)[::3]
+    short = sum(_steady_chain(mj.mojette_schedule(plan, m), 8) <= 3 for m in masks)
+    assert short >= 0.7 * len(masks), (short, len(masks))
+
+
 # ---- decode_lines' shared-memory layout (mojette_schedule_layout) ------------
 
 def _bank_model_cost(P, Q, p, sched, phase, orders, rev):
