@@ -659,6 +659,17 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
             if constexpr (PIPE) return oa[k];
             else return opaddr(k);
         };
+        // Q > 4: an operand outside the image is not loaded at all (a zero),
+        // instead of reading the zero word beside its row: fewer shared-memory
+        // accesses and bank conflicts where the kernel is bound by them
+        auto opload = [&](int k) -> uint64_t {
+            if constexpr (PIPE) {
+                return ld_s64(oa[k]);
+            } else {
+                const uint32_t c = (uint32_t)(x + dk[k]);
+                return ld_s64_if(REV ? rk[k] - 8u * c : rk[k] + 8u * c, c < (uint32_t)P);
+            }
+        };
         set_oa();
         // The step loop, compiled once per bound MC on the steady pattern's
         // longest same-step chain (steady steps run only the shuffle rounds
@@ -684,7 +695,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                         const uint64_t own = ld_s64(pos);
                         uint64_t lv[Q > 1 ? Q - 1 : 1];
 #pragma unroll
-                        for (int k = 0; k < Q - 1; ++k) lv[k] = ld_s64(addr(k));
+                        for (int k = 0; k < Q - 1; ++k) lv[k] = opload(k);
                         const uint32_t at = pos;
                         pos += stepb;
                         if constexpr (FAST) {
@@ -771,7 +782,7 @@ __global__ void __launch_bounds__(32) decode_lines(const __grid_constant__ DecPa
                 if (act) {
                     own = ld_s64(pos);
 #pragma unroll
-                    for (int k = 0; k < Q - 1; ++k) v ^= ld_s64(addr(k));
+                    for (int k = 0; k < Q - 1; ++k) v ^= opload(k);
                 }
                 // segmented suffix XOR: v_l ^= v_{l+1} while linked (only the
                 // rounds the step's longest chain needs)
