@@ -24,9 +24,10 @@
 //     bounds test sits in the inner loop.
 // decode_lines, the default path kernel, keeps each stripe in its own region
 // with rows in the order of the bins it stages (one bulk copy per front's run
-// of bins), one zero word beside each row (operand columns outside the image
-// are clamped to it), and a per-path bank layout chosen on the host (row
-// phases and per-front load orders). decode_fronts, decode_cols and
+// of bins), one zero word beside each row (at Q <= 4 operand columns outside
+// the image are clamped to it; at Q > 4 such operands are not loaded), and
+// a per-path bank layout chosen on the host (row phases and per-front load
+// orders). decode_fronts, decode_cols and
 // decode_stream interleave the G stripes of a warp word by word, staged by
 // 8-byte cp.async into rows with zero columns around them.
 //
@@ -337,9 +338,11 @@ __global__ void __launch_bounds__(32) decode_fronts(const __grid_constant__ DecP
 // line l+1, which line l+1 may rebuild in this same step. Those same-step
 // links (bit 2l+side of the step's forward word) form chains l -> l+1 -> ...
 // within a front; the chain values are a segmented suffix XOR over the lines,
-// done with log2(Q) rounds of warp shuffles, so every lane of every line
-// works at every step and a step costs one shared-memory round trip. The
-// layout, the staging and the addressing are described in the kernel.
+// done with warp shuffles (only the rounds the path's chains need), so every
+// lane of every line works at every step and a step costs one shared-memory
+// round trip. At Q <= 4 a run of steady steps (every front moves, one link
+// pattern) runs as an inner loop with no step-table reads. The layout, the
+// staging and the addressing are described in the kernel.
 //
 // SYS: the systematic form. The lines rebuilt are the lost data lines (Q of
 // them, at image rows lpos[]) of the data buffer (img, or dstp[s] batched, Qd
