@@ -271,12 +271,16 @@ int mojette_decode_noalloc(mojette_plan_t plan, const uint64_t *d_proj,
  *   6 decode_ilv     the path of Sec. 2.2 with the stripes across the lanes
  *                    (one lane per stripe, front and half of the lines;
  *                    non-systematic, Q <= 8);
+ *   7 decode_ring    the path of Sec. 2.2 swept from the left end only, each
+ *                    (stripe, line) held as a ring of 64 or 128 words
+ *                    (non-systematic, untrimmed, Q <= 8, where the host's
+ *                    replay of the path shows it fits a ring);
  *  -1                no launch (a systematic mask with no data line lost).
  * The default is the paper's inverse: decode_lines up to 8 lines,
  * decode_fronts beyond, and for a systematic plan decode_lines over the lost
  * lines or decode_scan2 for two of them. The MOJETTE_DECODE_KERNEL
- * environment variable may name another kernel (lines, ilv, fronts, stream,
- * cols, scan, vander) where it applies; a stripe too wide for the chosen
+ * environment variable may name another kernel (lines, ilv, ring, fronts,
+ * stream, cols, scan, vander) where it applies; a stripe too wide for the chosen
  * kernel's shared memory falls back to decode_lines, then decode_fronts, at
  * launch. Errors: -EINVAL, -ENOTRECOVERABLE, -ENOMEM.
  */
